@@ -1,0 +1,637 @@
+"""FP64 CPU oracle of the double-distribution quasi-equilibrium DVBM time step.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this module.
+The product path (the CUDA library and its binding) never calls it and shares no
+code with it.
+
+What it computes (Strässle, Hosseini & Karlin, "Consistent kinetic modeling of
+compressible flows with variable Prandtl numbers: double-distribution
+quasi-equilibrium approach"):
+
+* the D2Q25 Gauss--Hermite lattice (App. G, Table "D2Q25"),
+* moments of the populations (Sec. II.D.1, Eqs. eq_quadratur1-3) with the
+  internal non-translational energy split (II), temperature from the total
+  energy (Eq. Total_energy_MB),
+* relaxation times from mu and Pr (Sec. II.C, Eqs. visc_shear_1/2,
+  Pr_times_cases),
+* Grad--Hermite equilibria (Sec. II.D.2, Eq. Grad_g; App. D) for f to fourth
+  order and g to second order (Sec. II.D.3, App. E),
+* quasi-equilibria from the moment sets of Table I (split II rows) converted to
+  Hermite coefficients with the semi-recursive formulas (App. D,
+  Eq. Hermitecoefficients-static-regform),
+* the explicit finite-volume update (Sec. III.A.1, Eq. finalDiscretePDE) with
+  NND face reconstruction and the generalized limiter phi(a, b)
+  (Sec. III.A.2),
+* boundary ghost cells: periodic, zero-gradient ("von Neumann", Sec. III.A.3)
+  and the isothermal no-slip wall by ghost node + non-equilibrium
+  extrapolation (Sec. III.E),
+* equilibrium initial conditions and the CFL time step (Sec. III.A.3).
+
+Everything is plain PyTorch CPU float64 arithmetic vectorised over cells; the
+Hermite sums run over every index tuple of the full tensors, written from the
+definitions and not from any factorised form.  Because it is written with
+differentiable torch ops, ``torch.autograd`` applied to it gives the exact
+gradient of the discrete map (the discrete adjoint), which the tests use as
+the adjoint oracle.
+
+Readings of the paper where it is silent or garbled are listed in the design doc
+(the D2Q25 weights carry a /60; the third-order QE moment is the symmetric
+tensor whose contraction equals the heat-flux constraint; b = 0 gives a zero
+limited slope; the time step is fixed from the initial field).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+DT = torch.float64
+D = 2  # physical dimension
+
+# ---------------------------------------------------------------------------
+# Lattice (App. G, Table "D2Q25"; App. C for the Gauss--Hermite construction)
+# ---------------------------------------------------------------------------
+
+
+class Lattice:
+    """D2Q25 tensor-product Gauss--Hermite velocity set.
+
+    App. G, Table "D2Q25 (Hermite) for T_ref = 1": the five 1-D abscissae are
+    0, +-sqrt(5 - sqrt(10)), +-sqrt(5 + sqrt(10)) (roots of He_5) and the 2-D
+    weights are products of 1-D weights.  The table prints the 1-D weights as
+    8/15 and (7 +- 2 sqrt(10)) without their common denominator; the 1-D
+    Gauss--Hermite weights of He_5 are 8/15 and (7 +- 2 sqrt(10))/60 (they sum
+    to one).  Velocities scale with sqrt(R T_ref).
+
+    The oracle's own population order: x-node index p over ascending
+    abscissae, y-node index q likewise, population i = 5 p + q.
+    """
+
+    def __init__(self, R: float = 1.0, T_ref: float = 1.0):
+        s10 = math.sqrt(10.0)
+        a1 = math.sqrt(5.0 - s10)
+        a2 = math.sqrt(5.0 + s10)
+        xi = [-a2, -a1, 0.0, a1, a2]
+        w1 = [(7.0 - 2.0 * s10) / 60.0, (7.0 + 2.0 * s10) / 60.0, 8.0 / 15.0,
+              (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0]
+        self.R = float(R)
+        self.T_ref = float(T_ref)
+        self.c2 = self.R * self.T_ref  # R T_ref, the Hermite scale
+        c = math.sqrt(self.c2)
+        vx, vy, w = [], [], []
+        for p in range(5):
+            for q in range(5):
+                vx.append(c * xi[p])
+                vy.append(c * xi[q])
+                w.append(w1[p] * w1[q])
+        self.Q = 25
+        self.vx = torch.tensor(vx, dtype=DT)
+        self.vy = torch.tensor(vy, dtype=DT)
+        self.w = torch.tensor(w, dtype=DT)
+        self.xi1 = xi
+        self.w1 = w1
+
+    def v(self, alpha: int) -> torch.Tensor:
+        return self.vx if alpha == 0 else self.vy
+
+
+def _delta(a: int, b: int) -> float:
+    return 1.0 if a == b else 0.0
+
+
+def tuples(n: int):
+    """All index tuples (alpha_1..alpha_n) in {x=0, y=1}^n (full tensors)."""
+    return list(itertools.product((0, 1), repeat=n))
+
+
+# ---------------------------------------------------------------------------
+# Hermite polynomial tensors, App. D Eq. Hermitepolynomials-0-4
+# ---------------------------------------------------------------------------
+
+
+def hermite(lat: Lattice, tup) -> torch.Tensor:
+    """H_n(v_i) for one index tuple, evaluated at all Q velocities.
+
+    H_0 = 1, H_a = v_a, H_ab = v_a v_b - RT_ref d_ab,
+    H_abc = v_a v_b v_c - RT_ref [v_a d_bc]_cyc,
+    H_abcd = v_a v_b v_c v_d - RT_ref [v_a v_b d_cd]_cyc + (RT_ref)^2 [d_ab d_cd]_cyc,
+    where [.]_cyc runs over the distinct placements of the indices.
+    """
+    c2 = lat.c2
+    n = len(tup)
+    V = [lat.v(a) for a in tup]
+    if n == 0:
+        return torch.ones(lat.Q, dtype=DT)
+    if n == 1:
+        return V[0].clone()
+    d = lambda i, j: _delta(tup[i], tup[j])
+    if n == 2:
+        return V[0] * V[1] - c2 * d(0, 1)
+    if n == 3:
+        return (V[0] * V[1] * V[2]
+                - c2 * (V[0] * d(1, 2) + V[1] * d(0, 2) + V[2] * d(0, 1)))
+    if n == 4:
+        pairs = [(0, 1, 2, 3), (0, 2, 1, 3), (0, 3, 1, 2), (1, 2, 0, 3), (1, 3, 0, 2), (2, 3, 0, 1)]
+        cyc_vvd = sum(V[i] * V[j] * d(k, l) for (i, j, k, l) in pairs)
+        cyc_dd = d(0, 1) * d(2, 3) + d(0, 2) * d(1, 3) + d(0, 3) * d(1, 2)
+        return V[0] * V[1] * V[2] * V[3] - c2 * cyc_vvd + c2 * c2 * cyc_dd
+    raise ValueError("order > 4 not used")
+
+
+# ---------------------------------------------------------------------------
+# Moments of populations (Table I notation: M_n = sum_i v_i^{(x)n} f_i)
+# ---------------------------------------------------------------------------
+
+
+def lattice_moment(lat: Lattice, F: torch.Tensor, tup) -> torch.Tensor:
+    """M_tup(F) = sum_i v_{i,a1} ... v_{i,an} F_i  (F has shape [Q, ...])."""
+    wgt = torch.ones(lat.Q, dtype=DT)
+    for a in tup:
+        wgt = wgt * lat.v(a)
+    return torch.einsum("i,i...->...", wgt, F)
+
+
+@dataclass
+class Params:
+    """Model parameters.  Pr, gamma, mu may be python floats or 0-d tensors
+    (tensors are used by the tests to differentiate with respect to them)."""
+    Pr: object = 0.71
+    gamma: object = 1.4
+    mu: object = 5e-5
+    R: float = 1.0
+    T_ref: float = 1.0
+    beta: float = 1.2  # limiter parameter, Sec. III.A.3
+
+    def Cv(self):
+        return self.R / (self.gamma - 1.0)
+
+
+def macroscopic(lat: Lattice, P: Params, f: torch.Tensor, g: torch.Tensor):
+    """rho, rho u, E (split II) and T (Sec. II.D.1 Eqs. eq_quadratur1-3;
+    Eq. Total_energy_MB: E = rho C_v T + rho u^2 / 2)."""
+    rho = f.sum(0)
+    jx = torch.einsum("i,i...->...", lat.vx, f)
+    jy = torch.einsum("i,i...->...", lat.vy, f)
+    v2 = lat.vx * lat.vx + lat.vy * lat.vy
+    E = g.sum(0) + torch.einsum("i,i...->...", 0.5 * v2, f)
+    ux = jx / rho
+    uy = jy / rho
+    T = (E / rho - 0.5 * (ux * ux + uy * uy)) / P.Cv()
+    return rho, ux, uy, T, E
+
+
+def relaxation_times(P: Params, rho, T):
+    """tau_1, tau_2 from mu and Pr (Sec. II.C):
+    Pr <= 1: nu = mu/rho = tau_1 R T and Pr = tau_1/tau_2;
+    Pr >= 1: nu = mu/rho = tau_2 R T and Pr = tau_2/tau_1."""
+    p = rho * P.R * T
+    if float(P.Pr) <= 1.0:
+        tau1 = P.mu / p
+        tau2 = tau1 / P.Pr
+    else:
+        tau2 = P.mu / p
+        tau1 = tau2 / P.Pr
+    return tau1, tau2
+
+
+# ---------------------------------------------------------------------------
+# Hermite coefficients
+# ---------------------------------------------------------------------------
+
+
+def a_eq_f(lat: Lattice, rho, u, T, tup):
+    """Equilibrium coefficients of f written out with theta = T/T_ref
+    (App. D, Eq. Hermitecoefficients-feq-writtenout-static)."""
+    c2 = lat.c2
+    th1 = T / lat.T_ref - 1.0
+    n = len(tup)
+    U = [u[a] for a in tup]
+    d = lambda i, j: _delta(tup[i], tup[j])
+    if n == 0:
+        return rho
+    if n == 1:
+        return rho * U[0]
+    if n == 2:
+        return rho * U[0] * U[1] + c2 * th1 * rho * d(0, 1)
+    if n == 3:
+        return (rho * U[0] * U[1] * U[2]
+                + c2 * th1 * rho * (U[0] * d(1, 2) + U[1] * d(0, 2) + U[2] * d(0, 1)))
+    if n == 4:
+        pairs = [(0, 1, 2, 3), (0, 2, 1, 3), (0, 3, 1, 2), (1, 2, 0, 3), (1, 3, 0, 2), (2, 3, 0, 1)]
+        cyc_uud = sum(U[i] * U[j] * d(k, l) for (i, j, k, l) in pairs)
+        cyc_dd = d(0, 1) * d(2, 3) + d(0, 2) * d(1, 3) + d(0, 3) * d(1, 2)
+        return (rho * U[0] * U[1] * U[2] * U[3] + c2 * th1 * rho * cyc_uud
+                + c2 * c2 * th1 * th1 * rho * cyc_dd)
+    raise ValueError
+
+
+def maxwell_moment(lat: Lattice, R: float, rho, u, T, tup):
+    """Moments of the Maxwell--Boltzmann equilibrium up to order four
+    (App. A, Eq. f-equilibria-moments-MB)."""
+    n = len(tup)
+    U = [u[a] for a in tup]
+    d = lambda i, j: _delta(tup[i], tup[j])
+    RT = R * T
+    if n == 0:
+        return rho
+    if n == 1:
+        return rho * U[0]
+    if n == 2:
+        return rho * U[0] * U[1] + rho * RT * d(0, 1)
+    if n == 3:
+        return rho * U[0] * U[1] * U[2] + rho * RT * (U[0] * d(1, 2) + U[1] * d(0, 2) + U[2] * d(0, 1))
+    if n == 4:
+        pairs = [(0, 1, 2, 3), (0, 2, 1, 3), (0, 3, 1, 2), (1, 2, 0, 3), (1, 3, 0, 2), (2, 3, 0, 1)]
+        cyc_uud = sum(U[i] * U[j] * d(k, l) for (i, j, k, l) in pairs)
+        cyc_dd = d(0, 1) * d(2, 3) + d(0, 2) * d(1, 3) + d(0, 3) * d(1, 2)
+        return rho * U[0] * U[1] * U[2] * U[3] + rho * RT * cyc_uud + rho * RT * RT * cyc_dd
+    raise ValueError
+
+
+def g_eq_moment(P: Params, rho, u, T, tup):
+    """Equilibrium moments of g for split II (App. A):
+    int g^eq = rho (C_v T - R T D/2), int v_a g^eq = rho (C_v T - R T D/2) u_a,
+    int v_a v_b g^eq = rho (C_v T - R T D/2)(u_a u_b + R T d_ab)."""
+    eps = P.Cv() * T - P.R * T * D / 2.0
+    n = len(tup)
+    if n == 0:
+        return rho * eps
+    if n == 1:
+        return rho * eps * u[tup[0]]
+    if n == 2:
+        return rho * eps * (u[tup[0]] * u[tup[1]] + P.R * T * _delta(tup[0], tup[1]))
+    raise ValueError
+
+
+def coefficients_from_moments(lat: Lattice, M: dict, N: int) -> dict:
+    """Hermite coefficient tensors from arbitrary moments, semi-recursive form
+    (App. D, Eq. Hermitecoefficients-static-regform):
+    a_0 = M_0, a_a = M_a, a_ab = M_ab - RT_ref a_0 d_ab,
+    a_abc = M_abc - RT_ref [a_a d_bc]_cyc,
+    a_abcd = M_abcd - RT_ref [a_ab d_cd]_cyc - (RT_ref)^2 a_0 [d_ab d_cd]_cyc.
+    ``M`` maps index tuples to moment fields."""
+    c2 = lat.c2
+    a = {}
+    a[()] = M[()]
+    if N >= 1:
+        for t in tuples(1):
+            a[t] = M[t]
+    if N >= 2:
+        for t in tuples(2):
+            a[t] = M[t] - c2 * a[()] * _delta(t[0], t[1])
+    if N >= 3:
+        for t in tuples(3):
+            a[t] = M[t] - c2 * (a[(t[0],)] * _delta(t[1], t[2]) + a[(t[1],)] * _delta(t[0], t[2])
+                                + a[(t[2],)] * _delta(t[0], t[1]))
+    if N >= 4:
+        pairs = [(0, 1, 2, 3), (0, 2, 1, 3), (0, 3, 1, 2), (1, 2, 0, 3), (1, 3, 0, 2), (2, 3, 0, 1)]
+        for t in tuples(4):
+            cyc = sum(a[(t[i], t[j])] * _delta(t[k], t[l]) for (i, j, k, l) in pairs)
+            cyc_dd = (_delta(t[0], t[1]) * _delta(t[2], t[3]) + _delta(t[0], t[2]) * _delta(t[1], t[3])
+                      + _delta(t[0], t[3]) * _delta(t[1], t[2]))
+            a[t] = M[t] - c2 * cyc - c2 * c2 * a[()] * cyc_dd
+    return a
+
+
+def grad_expansion(lat: Lattice, a: dict, N: int) -> torch.Tensor:
+    """Finite Grad--Hermite expansion (Sec. II.D.2 Eq. Grad_g; App. D
+    Eq. Grad-Hermite-expansion-static):
+    F_i = w_i sum_{n<=N} 1/(n! (R T_ref)^n) a_n : H_n(v_i),
+    with the full contraction over every index tuple."""
+    out = None
+    for n in range(N + 1):
+        fac = 1.0 / (math.factorial(n) * lat.c2 ** n)
+        for t in tuples(n):
+            H = hermite(lat, t)
+            term = (fac * H).view([lat.Q] + [1] * a[t].dim()) * a[t].unsqueeze(0)
+            out = term if out is None else out + term
+    return lat.w.view([lat.Q] + [1] * (out.dim() - 1)) * out
+
+
+# ---------------------------------------------------------------------------
+# Equilibria and quasi-equilibria (Table I, split II)
+# ---------------------------------------------------------------------------
+
+
+def equilibria(lat: Lattice, P: Params, rho, ux, uy, T):
+    """f^eq (N = 4, theta-form coefficients) and g^eq (N = 2, coefficients from
+    the g^eq moments through the semi-recursive formulas).  Orders from
+    Sec. II.D.3 / App. E for split II."""
+    u = (ux, uy)
+    af = {t: a_eq_f(lat, rho, u, T, t) for n in range(5) for t in tuples(n)}
+    feq = grad_expansion(lat, af, 4)
+    Mg = {t: g_eq_moment(P, rho, u, T, t) for n in range(3) for t in tuples(n)}
+    ag = coefficients_from_moments(lat, Mg, 2)
+    geq = grad_expansion(lat, ag, 2)
+    return feq, geq
+
+
+def _S_operator(u, A, tup):
+    """Symmetric third-order tensor S(u, A)_abc = [u_a A_bc]_cyc
+    - tr(A)/(D+2) [u_a d_bc]_cyc whose contraction over (b, c) equals 2 (A u)_a.
+    This is the reading of the tensor "2 u (x) A" in Table I (split II, third
+    order of f*): the heat-flux constraints (Eqs. QE_Pr<1_quasiconserved,
+    QE_Pr>1_conserved) fix only its contraction 2 (A u)_a."""
+    a, b, c = tup
+    trA = A[(0, 0)] + A[(1, 1)]
+    cyc_uA = u[a] * A[(b, c)] + u[b] * A[(a, c)] + u[c] * A[(a, b)]
+    cyc_ud = u[a] * _delta(b, c) + u[b] * _delta(a, c) + u[c] * _delta(a, b)
+    return cyc_uA - trA / (D + 2.0) * cyc_ud
+
+
+def quasi_equilibria(lat: Lattice, P: Params, f, g, rho, ux, uy, T, feq, geq):
+    """f* and g* for split II from the moment sets of Table I:
+
+    Pr < 1: f* keeps M_0, M_1, M_2, M_4 of f^eq and takes
+            M_3(f) - 2 u (x) (M_2(f) - M_2(f^eq)); g* keeps M_0, M_2 of g^eq and
+            takes M_1(g).
+    Pr > 1: f* takes M_2(f) - (I/D) tr(M_2(f) - M_2(f^eq)) and
+            M_3(f^eq) + 2 u (x) [Delta - (I/D) tr Delta] and keeps M_0, M_1, M_4
+            of f^eq; g* = g^eq.
+    Pr = 1: f* = f^eq, g* = g^eq.
+
+    Moments M_n(.) are lattice sums (Table I notation); target moments are
+    converted to Hermite coefficients with the semi-recursive formulas.
+    """
+    Pr = float(P.Pr)
+    if Pr == 1.0:
+        return feq, geq
+    u = (ux, uy)
+    Mf = {t: lattice_moment(lat, f, t) for n in range(4) for t in tuples(n)}
+    Meq = {t: lattice_moment(lat, feq, t) for n in range(5) for t in tuples(n)}
+    Delta = {t: Mf[t] - Meq[t] for t in tuples(2)}
+    Mstar = {}
+    for n in (0, 1):
+        for t in tuples(n):
+            Mstar[t] = Meq[t]
+    for t in tuples(4):
+        Mstar[t] = Meq[t]
+    if Pr < 1.0:
+        for t in tuples(2):
+            Mstar[t] = Meq[t]
+        for t in tuples(3):
+            Mstar[t] = Mf[t] - _S_operator(u, Delta, t)
+    else:
+        trD = Delta[(0, 0)] + Delta[(1, 1)]
+        for t in tuples(2):
+            Mstar[t] = Mf[t] - _delta(t[0], t[1]) / D * trD
+        Dp = {t: Delta[t] - _delta(t[0], t[1]) / D * trD for t in tuples(2)}
+        for t in tuples(3):
+            Mstar[t] = Meq[t] + _S_operator(u, Dp, t)
+    astar = coefficients_from_moments(lat, Mstar, 4)
+    fstar = grad_expansion(lat, astar, 4)
+    if Pr < 1.0:
+        Mg = {t: lattice_moment(lat, geq, t) for n in range(3) for t in tuples(n)}
+        for t in tuples(1):
+            Mg[t] = lattice_moment(lat, g, t)
+        ag = coefficients_from_moments(lat, Mg, 2)
+        gstar = grad_expansion(lat, ag, 2)
+    else:
+        gstar = geq
+    return fstar, gstar
+
+
+# ---------------------------------------------------------------------------
+# Flux reconstruction (Sec. III.A.2)
+# ---------------------------------------------------------------------------
+
+
+def limiter_phi(a, b, beta):
+    """phi(a, b) = max(0, min(beta a/b, (1 + a/b)/2, beta)), Sec. III.A.2."""
+    r = a / b
+    return torch.clamp(torch.minimum(torch.minimum(beta * r, 0.5 * (1.0 + r)),
+                                     torch.full_like(r, beta)), min=0.0)
+
+
+def half_b_phi(a, b, beta):
+    """The term (b/2) phi(a, b) of the NND face value.  At b = 0 the ratio is
+    undefined; phi is bounded, so the term is taken as 0 there."""
+    zero = b == 0
+    bs = torch.where(zero, torch.ones_like(b), b)
+    val = 0.5 * bs * limiter_phi(a, bs, beta)
+    return torch.where(zero, torch.zeros_like(val), val)
+
+
+def face_values(Fm2, Fm1, F0, Fp1, vpos, beta):
+    """NND interface value at sigma = x - dx/2 between cells (x - dx) and x.
+
+    v >= 0: F_face = F_{x-dx} + b/2 phi(a, b), a = F_{x-dx} - F_{x-2dx}, b = F_x - F_{x-dx};
+    v <  0: F_face = F_x + b/2 phi(a, b),      a = F_x - F_{x+dx},      b = F_{x-dx} - F_x.
+    ``vpos`` is a [Q] bool tensor (v_i . n >= 0)."""
+    a_p = Fm1 - Fm2
+    b_p = F0 - Fm1
+    pos = Fm1 + half_b_phi(a_p, b_p, beta)
+    a_n = F0 - Fp1
+    b_n = Fm1 - F0
+    neg = F0 + half_b_phi(a_n, b_n, beta)
+    sel = vpos.view([-1] + [1] * (F0.dim() - 1))
+    return torch.where(sel, pos, neg)
+
+
+# ---------------------------------------------------------------------------
+# Boundary conditions: ghost layers (2 per side)
+# ---------------------------------------------------------------------------
+
+PERIODIC, ZEROGRAD, WALL = 0, 1, 2
+
+
+@dataclass
+class BC:
+    kind: int = PERIODIC
+    u_wall: tuple = (0.0, 0.0)
+    T_wall: float = 1.0
+
+
+@dataclass
+class Grid:
+    Nx: int
+    Ny: int
+    Lx: float = 1.0
+    Ly: float = 1.0
+    bcs: tuple = field(default_factory=lambda: (BC(), BC(), BC(), BC()))  # xlo, xhi, ylo, yhi
+
+    @property
+    def dx(self):
+        return self.Lx / self.Nx
+
+    @property
+    def dy(self):
+        return self.Ly / self.Ny
+
+
+def _wall_ghost(lat, P, fB, gB, bc: BC):
+    """Ghost node + non-equilibrium extrapolation (Sec. III.E):
+    rho_G = rho_B, u_G = 2 u_W - u_B, T_G = 2 T_W - T_B,
+    f_G = f^eq(rho_G, u_G, T_G) + (f_B - f^eq(rho_B, u_B, T_B)), likewise g."""
+    rho, ux, uy, T, _ = macroscopic(lat, P, fB, gB)
+    feqB, geqB = equilibria(lat, P, rho, ux, uy, T)
+    feqG, geqG = equilibria(lat, P, rho, 2.0 * bc.u_wall[0] - ux, 2.0 * bc.u_wall[1] - uy,
+                            2.0 * bc.T_wall - T)
+    return feqG + (fB - feqB), geqG + (gB - geqB)
+
+
+def pad_axis(lat, P, f, g, axis, lo: BC, hi: BC):
+    """Add two ghost layers on both ends of ``axis`` (1 = y, 2 = x) of the
+    [Q, Ny, Nx] population arrays.  Periodic: wrap; zero-gradient: both ghosts
+    copy the boundary cell; wall: ghost k mirrors interior cell k (k = 1, 2)
+    about the wall face (the reading of the two-layer ghost node)."""
+    n = f.shape[axis]
+
+    def take(A, i):
+        return A.narrow(axis, i, 1)
+
+    def ghosts(side: BC, lower: bool):
+        if side.kind == PERIODIC:
+            idx = [n - 2, n - 1] if lower else [0, 1]
+            return ([take(f, i) for i in idx], [take(g, i) for i in idx])
+        if side.kind == ZEROGRAD:
+            b = 0 if lower else n - 1
+            return ([take(f, b), take(f, b)], [take(g, b), take(g, b)])
+        if side.kind == WALL:
+            # interior cells B1 (adjacent to wall) and B2; ghosts G1, G2 mirror them
+            b1, b2 = (0, 1) if lower else (n - 1, n - 2)
+            fg1, gg1 = _wall_ghost(lat, P, take(f, b1), take(g, b1), side)
+            fg2, gg2 = _wall_ghost(lat, P, take(f, b2), take(g, b2), side)
+            if lower:  # order along the axis: G2, G1 | interior
+                return ([fg2, fg1], [gg2, gg1])
+            return ([fg1, fg2], [gg1, gg2])
+        raise ValueError(side.kind)
+
+    lf, lg = ghosts(lo, True)
+    hf, hg = ghosts(hi, False)
+    fp = torch.cat(lf + [f] + hf, dim=axis)
+    gp = torch.cat(lg + [g] + hg, dim=axis)
+    return fp, gp
+
+
+def _check_bcs(grid: Grid):
+    xlo, xhi, ylo, yhi = grid.bcs
+    if (xlo.kind == PERIODIC) != (xhi.kind == PERIODIC) or (ylo.kind == PERIODIC) != (yhi.kind == PERIODIC):
+        raise ValueError("periodic boundaries must come in pairs")
+
+
+# ---------------------------------------------------------------------------
+# Time step (Sec. III.A.1, Eq. finalDiscretePDE)
+# ---------------------------------------------------------------------------
+
+
+def advective_term(lat, P, grid: Grid, fpx, fpy):
+    """(dt/dV) sum_sigma F_i(sigma) / dt, i.e. (1/dV) sum over the four faces of
+    v_i . n(sigma) F_face dA(sigma), from the x-padded [Q, Ny, Nx+4] and the
+    y-padded [Q, Ny+4, Nx] arrays (Sec. III.A.2 flux definition)."""
+    Nx, Ny = grid.Nx, grid.Ny
+    beta = P.beta
+    # x-faces k - 1/2 for k = 0..Nx (padded index k + 2)
+    def sx(o):  # cells shifted along x: padded columns [o, o + Nx + 1)
+        return fpx[:, :, o:o + Nx + 1]
+    Fx = face_values(sx(0), sx(1), sx(2), sx(3), lat.vx >= 0, beta)  # faces 0..Nx
+    def sy(o):
+        return fpy[:, o:o + Ny + 1, :]
+    Fy = face_values(sy(0), sy(1), sy(2), sy(3), lat.vy >= 0, beta)
+    dV = grid.dx * grid.dy
+    vx = lat.vx.view(-1, 1, 1)
+    vy = lat.vy.view(-1, 1, 1)
+    # outward normals: +x on face j+1/2, -x on face j-1/2; dA = dy for x-faces, dx for y-faces
+    flux_sum = (vx * Fx[:, :, 1:] * grid.dy - vx * Fx[:, :, :-1] * grid.dy
+                + vy * Fy[:, 1:, :] * grid.dx - vy * Fy[:, :-1, :] * grid.dx)
+    return flux_sum / dV
+
+
+def step(lat: Lattice, P: Params, grid: Grid, f, g, dt):
+    """One explicit Euler step, Eq. finalDiscretePDE:
+    F(t+dt) = F - (dt/dV) sum_sigma Flux - (dt/tau_1)(F - F*) - (dt/tau_2)(F* - F^eq)
+    for F in {f_i, g_i}, everything evaluated at time t."""
+    _check_bcs(grid)
+    xlo, xhi, ylo, yhi = grid.bcs
+    fpx, gpx = pad_axis(lat, P, f, g, 2, xlo, xhi)
+    fpy, gpy = pad_axis(lat, P, f, g, 1, ylo, yhi)
+    rho, ux, uy, T, _ = macroscopic(lat, P, f, g)
+    tau1, tau2 = relaxation_times(P, rho, T)
+    feq, geq = equilibria(lat, P, rho, ux, uy, T)
+    fstar, gstar = quasi_equilibria(lat, P, f, g, rho, ux, uy, T, feq, geq)
+    adv_f = advective_term(lat, P, grid, fpx, fpy)
+    adv_g = advective_term(lat, P, grid, gpx, gpy)
+    f_new = f - dt * adv_f - (dt / tau1) * (f - fstar) - (dt / tau2) * (fstar - feq)
+    g_new = g - dt * adv_g - (dt / tau1) * (g - gstar) - (dt / tau2) * (gstar - geq)
+    return f_new, g_new
+
+
+def step_patch(lat: Lattice, P: Params, grid: Grid, fpatch, gpatch, dt):
+    """Update of the single centre cell of 5x5 patches [Q, B, 5, 5] whose
+    cross-shaped neighbourhood holds the values the scheme reads (neighbours at
+    distance 1 and 2 along x and y).  Used to check single cells of large runs.
+    Returns [Q, B] for f and g."""
+    f = fpatch[:, :, 2, 2]
+    g = gpatch[:, :, 2, 2]
+    rho, ux, uy, T, _ = macroscopic(lat, P, f, g)
+    tau1, tau2 = relaxation_times(P, rho, T)
+    feq, geq = equilibria(lat, P, rho, ux, uy, T)
+    fstar, gstar = quasi_equilibria(lat, P, f, g, rho, ux, uy, T, feq, geq)
+    beta = P.beta
+    dV = grid.dx * grid.dy
+    vx = lat.vx.view(-1, 1)
+    vy = lat.vy.view(-1, 1)
+
+    def adv(Pt):
+        row = Pt[:, :, 2, :]  # along x: columns 0..4
+        col = Pt[:, :, :, 2]  # along y
+        fxl = face_values(row[..., 0], row[..., 1], row[..., 2], row[..., 3], lat.vx >= 0, beta)
+        fxr = face_values(row[..., 1], row[..., 2], row[..., 3], row[..., 4], lat.vx >= 0, beta)
+        fyl = face_values(col[..., 0], col[..., 1], col[..., 2], col[..., 3], lat.vy >= 0, beta)
+        fyr = face_values(col[..., 1], col[..., 2], col[..., 3], col[..., 4], lat.vy >= 0, beta)
+        return (vx * fxr * grid.dy - vx * fxl * grid.dy + vy * fyr * grid.dx - vy * fyl * grid.dx) / dV
+
+    f_new = f - dt * adv(fpatch) - (dt / tau1) * (f - fstar) - (dt / tau2) * (fstar - feq)
+    g_new = g - dt * adv(gpatch) - (dt / tau1) * (g - gstar) - (dt / tau2) * (gstar - geq)
+    return f_new, g_new
+
+
+# ---------------------------------------------------------------------------
+# Initial conditions, time step size, diagnostics (Sec. III.A.3)
+# ---------------------------------------------------------------------------
+
+
+def init_populations(lat: Lattice, P: Params, rho, ux, uy, T):
+    """Initial conditions supplied as equilibrium populations (Sec. III.A.3)
+    at the cell-centre values of the given fields."""
+    return equilibria(lat, P, rho, ux, uy, T)
+
+
+def cfl_dt(P: Params, grid: Grid, ux, uy, T, cfl: float):
+    """dt = CFL min(dx, dy) / (|u| + c_s), Sec. III.A.3, with the maximum of
+    |u| + sqrt(gamma R T) over the initial field (reading: global, fixed)."""
+    speed = torch.sqrt(ux * ux + uy * uy) + torch.sqrt(float(P.gamma) * P.R * T)
+    return cfl * min(grid.dx, grid.dy) / float(speed.max())
+
+
+def totals(lat, P, grid: Grid, f, g):
+    """Domain totals of mass, x/y momentum and total energy (cell volume dV)."""
+    rho, ux, uy, T, E = macroscopic(lat, P, f, g)
+    dV = grid.dx * grid.dy
+    return (float(rho.sum()) * dV, float((rho * ux).sum()) * dV, float((rho * uy).sum()) * dV,
+            float(E.sum()) * dV)
+
+
+class Simulation:
+    """Convenience driver: equilibrium ICs, fixed dt, n steps, moments."""
+
+    def __init__(self, grid: Grid, P: Params, rho, ux, uy, T, cfl=0.01, dt=None):
+        self.lat = Lattice(P.R, P.T_ref)
+        self.P = P
+        self.grid = grid
+        self.f, self.g = init_populations(self.lat, P, rho, ux, uy, T)
+        self.dt = float(dt) if dt else cfl_dt(P, grid, ux, uy, T, cfl)
+        self.nsteps = 0
+
+    def run(self, n: int):
+        for _ in range(n):
+            self.f, self.g = step(self.lat, self.P, self.grid, self.f, self.g, self.dt)
+            self.nsteps += 1
+        return self
+
+    def fields(self):
+        rho, ux, uy, T, _ = macroscopic(self.lat, self.P, self.f, self.g)
+        return rho, ux, uy, T

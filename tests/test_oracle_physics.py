@@ -1,0 +1,98 @@
+"""Physics pins of the oracle: dissipation rates against the Navier--Stokes--
+Fourier closed forms of Sec. II.C (nu = mu/rho; alpha = nu/Pr for any Pr;
+zeta = (2/D - R/C_v) nu) and Galilean invariance under a uniform boost.
+
+Shear mode (Sec. III.D.1): u_y = A sin(k x) decays as exp(-nu k^2 t) exactly in
+linearised NSF.  Entropy mode (Sec. III.D.3): rho = 1 + A sin(k x), T = 1/rho
+couples weakly to acoustics, so the measured (rho, u_x, T) Fourier amplitudes
+are compared with the solution of the linearised 1-D NSF system
+    d/dt [rho', u', T'] = M [rho', u', T'],
+    M = [[0, -ik, 0], [-ik R, -nu_L k^2, -ik R], [0, -ik R/C_v, -gamma alpha k^2]]
+(rho0 = T0 = 1, nu_L = (2 - 2/D) nu + zeta) by a matrix exponential, with alpha
+fitted.  Tolerances cover explicit-Euler (~dt/2tau), 32-cell spatial and
+Burnett-order ((nu k/c)^2) errors of the discrete model; a wrong Pr or gamma
+mapping is off by tens of percent.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+import scipy.optimize as so
+import torch
+
+from oracle import dvbm_oracle as O
+
+DT = torch.float64
+
+
+def run_modes(Pr, gamma, Ma, Nx=32, Ny=2, mu=0.01, dt=2e-4, n1=600, n2=1000, amp=1e-4):
+    x = (np.arange(Nx) + 0.5) / Nx
+    rho = 1 + amp * np.sin(2 * np.pi * x)[None, :] + np.zeros((Ny, 1))
+    T = 1 / rho
+    u0 = Ma * math.sqrt(gamma)
+    ux = np.full((Ny, Nx), u0)
+    uy = amp * np.sin(2 * np.pi * x)[None, :] + np.zeros((Ny, 1))
+    t = lambda a: torch.tensor(a, dtype=DT)
+    P = O.Params(Pr=Pr, gamma=gamma, mu=mu)
+    s = O.Simulation(O.Grid(Nx, Ny, 1.0, Ny / Nx), P, t(rho), t(ux), t(uy), t(T), dt=dt)
+    e = np.exp(-2j * np.pi * x)
+
+    def coef():
+        r, ux_, uy_, T_ = [a.numpy().mean(0) for a in s.fields()]
+        ph = np.exp(2j * np.pi * u0 * s.nsteps * dt)  # undo mean-flow advection
+        return np.array([(r * e).mean() * ph, ((ux_ - u0) * e).mean() * ph, (uy_ * e).mean() * ph,
+                         (T_ * e).mean() * ph])
+
+    s.run(n1)  # let the non-hydrodynamic transient (a few tau) die out
+    c1 = coef()
+    t1 = s.nsteps * dt
+    hist = []
+    for _ in range(5):
+        s.run(n2 // 5)
+        hist.append((s.nsteps * dt - t1, coef()))
+    k = 2 * np.pi
+    R = 1.0
+    Cv = R / (gamma - 1)
+    nu = mu
+    nuL = (2 - 2 / 2) * nu + (2 / 2 - R / Cv) * nu
+
+    def M(alpha):
+        return np.array([[0, -1j * k, 0], [-1j * k * R, -nuL * k * k, -1j * k * R],
+                         [0, -1j * k * R / Cv, -gamma * alpha * k * k]])
+
+    def resid(p):
+        out = []
+        for (tt, c) in hist:
+            d = (sl.expm(M(p[0]) * tt) @ c1[[0, 1, 3]] - c[[0, 1, 3]]) / abs(c1[0])
+            out += [d.real, d.imag]
+        return np.concatenate(out)
+
+    alpha = so.least_squares(resid, [nu / Pr]).x[0]
+    nu_fit = -np.log(abs(hist[-1][1][2]) / abs(c1[2])) / hist[-1][0] / k ** 2
+    return nu_fit, alpha
+
+
+@pytest.mark.parametrize("Pr,gamma", [(0.5, 1.4), (1.0, 1.4), (2.0, 1.4), (0.71, 1.67)])
+def test_shear_and_thermal_dissipation_match_nsf(Pr, gamma):
+    nu_fit, alpha_fit = run_modes(Pr, gamma, 0.1)
+    nu = 0.01
+    assert abs(nu_fit / nu - 1) < 0.05, nu_fit
+    assert abs(alpha_fit / (nu / Pr) - 1) < 0.05, alpha_fit
+
+
+def test_rate_errors_shrink_under_refinement():
+    """The remaining deviation is spatial discretisation error: doubling the
+    resolution at Pr = 2 reduces both rate errors by more than 2x."""
+    e32 = run_modes(2.0, 1.4, 0.1, Nx=32)
+    e64 = run_modes(2.0, 1.4, 0.1, Nx=64)
+    for a, b, ref in zip(e32, e64, (0.01, 0.005)):
+        assert abs(b / ref - 1) < 0.5 * abs(a / ref - 1)
+
+
+def test_galilean_invariance_of_rates():
+    """Rates at Ma = 0 and Ma = 0.1 agree within 1 % (static lattice is only
+    approximately invariant, Sec. III.C-D)."""
+    a = run_modes(0.71, 1.4, 0.0)
+    b = run_modes(0.71, 1.4, 0.1)
+    assert abs(a[0] / b[0] - 1) < 0.01 and abs(a[1] / b[1] - 1) < 0.01

@@ -1,0 +1,156 @@
+/*
+ * dvbm.h -- C ABI of the GB300 double-distribution quasi-equilibrium DVBM
+ * time step (libdvbm.so).
+ *
+ * Model (Strässle, Hosseini & Karlin, double-distribution quasi-equilibrium
+ * approach): f (density/momentum) and g (internal non-translational energy,
+ * split II, Sec. II.B.3 Eq. energy_eq_1) populations on the D2Q25
+ * Gauss--Hermite lattice (App. G), fourth-order Grad--Hermite equilibria for f
+ * and second-order for g (Sec. II.D.2-3), quasi-equilibria from the Table I
+ * moment sets, two-rate relaxation (Eqs. new_collision_fi/gi) with
+ * tau_1, tau_2 from mu and Pr (Sec. II.C), explicit Euler finite-volume update
+ * with NND reconstruction and the generalized limiter (Sec. III.A.1-2,
+ * Eq. finalDiscretePDE).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns a dvbm_status and never aborts or throws.  On a
+ *    non-OK status a message is available from dvbm_last_error(ctx) (or
+ *    dvbm_last_error(NULL) for failures of dvbm_create).
+ *  - Macroscopic fields are row-major [Ny][Nx] double arrays (x fastest), cell
+ *    centres x_j = (j + 1/2) Lx/Nx, y_k = (k + 1/2) Ly/Ny.  The caller owns
+ *    every field buffer; the library owns the population buffers.
+ *  - on_device = 1: pointers are device pointers on the context's device; the
+ *    copies are stream-ordered on the context's stream.  on_device = 0: host
+ *    pointers; the call synchronises the stream before returning.
+ *  - A context is not thread-safe; calls on one context must be serialised.
+ *  - GPU work is issued on the CUDA stream given at creation (NULL = legacy
+ *    default stream).
+ */
+#ifndef DVBM_H
+#define DVBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dvbm_ctx dvbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  DVBM_OK = 0,
+  DVBM_EINVAL = 1,    /* invalid argument (null pointer, bad size or parameter) */
+  DVBM_ENOMEM = 2,    /* device allocation failed */
+  DVBM_ECUDA = 3,     /* a CUDA runtime call failed */
+  DVBM_EUNSTABLE = 4, /* a cell reached rho <= 0, T <= 0 or a non-finite value */
+  DVBM_ETIMEOUT = 5,  /* the stream did not finish within opts.timeout_s */
+  DVBM_ESTATE = 6     /* call not valid in the context's current state */
+} dvbm_status;
+
+/* Lattice / energy split.  Only D2Q25 with split II is built. */
+typedef enum { DVBM_D2Q25_SPLIT_II = 0 } dvbm_lattice;
+
+/* Population storage.  FP64: populations as doubles.  FP32DEV: populations
+ * stored as float deviations from w_i rho0 (f) and w_i rho0 (C_v - R) T0 (g);
+ * moments, temperature and equilibria are evaluated in double, advection in
+ * float on the deviations. */
+typedef enum { DVBM_FP64 = 0, DVBM_FP32DEV = 1 } dvbm_storage;
+
+/* Boundary kinds (Sec. III.A.3, Sec. III.E).  PERIODIC: wrap (must be set on
+ * both sides of an axis).  ZEROGRAD: zero-gradient ("von Neumann") ghost
+ * cells copying the boundary cell.  WALL: isothermal no-slip wall on the
+ * boundary face by ghost node + non-equilibrium extrapolation,
+ * rho_G = rho_B, u_G = 2 u_W - u_B, T_G = 2 T_W - T_B,
+ * f_G = f^eq(G) + (f_B - f^eq(B)) (same for g); ghost k mirrors interior
+ * cell k, k = 1, 2. */
+typedef enum { DVBM_BC_PERIODIC = 0, DVBM_BC_ZEROGRAD = 1, DVBM_BC_WALL = 2 } dvbm_bc_kind;
+
+typedef struct {
+  int kind;         /* dvbm_bc_kind */
+  double u_wall[2]; /* WALL: wall velocity */
+  double T_wall;    /* WALL: wall temperature */
+} dvbm_bc;
+
+/* Sides of the bcs[4] array passed to dvbm_create. */
+enum { DVBM_XLO = 0, DVBM_XHI = 1, DVBM_YLO = 2, DVBM_YHI = 3 };
+
+typedef struct {
+  double Lx, Ly;     /* domain size (default 1, Ny/Nx * Lx) */
+  double R;          /* specific gas constant (default 1, Sec. III.A.3) */
+  double T_ref;      /* lattice reference temperature (default 1, App. G) */
+  double rho0, T0;   /* FP32DEV reference state (default 1, 1) */
+  double beta;       /* limiter parameter in [1, 2] (default 1.2, Sec. III.A.3) */
+  double cfl;        /* CFL number of the time-step rule (default 0.01) */
+  double dt;         /* > 0: fixed time step overriding the CFL rule */
+  int check_every;   /* dvbm_step checks the instability flag every k steps
+                        (default 0: once at the end of each dvbm_step call;
+                        < 0: never) */
+  double timeout_s;  /* host wait limit for a check (default 600 s) */
+} dvbm_opts;
+
+/* Fill *opts with the defaults listed above (Lx = 1, Ly = 0 meaning
+ * Ny/Nx * Lx).  Returns DVBM_EINVAL for a null pointer. */
+dvbm_status dvbm_default_opts(dvbm_opts* opts);
+
+/* Create a context: validate parameters, allocate two population buffers
+ * (2 x 50 planes of (Ny + 4) x pitch values, ghost layers included) on the
+ * current CUDA device.  Pr > 0; 1 < gamma <= 2 (split II needs
+ * C_v >= R D/2, Sec. II.B.3); mu > 0; Nx, Ny >= 4; periodic sides paired.
+ * opts may be NULL (defaults).  stream: a cudaStream_t or NULL.
+ * Errors: EINVAL, ENOMEM, ECUDA; *out is NULL on failure. */
+dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, double Pr, double gamma,
+                        double mu, const dvbm_bc bcs[4], int storage, const dvbm_opts* opts,
+                        void* stream);
+
+/* Equilibrium initial conditions (Sec. III.A.3): populations = f^eq, g^eq of
+ * the given rho, u_x, u_y, T at the cell centres; fills ghost layers; fixes
+ * dt = cfl min(dx, dy) / max(|u| + sqrt(gamma R T)) over these fields unless
+ * opts.dt > 0.  Resets the step counter.  Errors: EINVAL (null pointer,
+ * rho <= 0 or T <= 0 or non-finite input: DVBM_EINVAL), ECUDA. */
+dvbm_status dvbm_init(dvbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                      const double* T, int on_device);
+
+/* Advance n >= 0 explicit Euler steps (Eq. finalDiscretePDE), asynchronously
+ * on the stream except for the instability checks (opts.check_every).
+ * Errors: ESTATE (not initialised), EUNSTABLE, ETIMEOUT, ECUDA. */
+dvbm_status dvbm_step(dvbm_ctx* ctx, int n);
+
+/* rho, u_x, u_y, T of the current state (Sec. II.D.1 moments, T from
+ * Eq. Total_energy_MB).  Any output pointer may be NULL to skip it. */
+dvbm_status dvbm_moments(dvbm_ctx* ctx, double* rho, double* ux, double* uy, double* T,
+                         int on_device);
+
+/* Domain totals out[0..3] = mass, x-momentum, y-momentum, total energy
+ * (sum over cells times dx dy).  Synchronous. */
+dvbm_status dvbm_totals(dvbm_ctx* ctx, double out[4]);
+
+/* Size in bytes of a state snapshot: 50 planes [c][Ny][Nx] of the storage
+ * type (double for FP64, float deviations for FP32DEV) plus one 8-byte step
+ * counter at the end.  Population order c = 5 p + q for f (c < 25) and
+ * 25 + 5 p + q for g, with x-node p and y-node q in the order
+ * (0, +sqrt(5 - sqrt 10), -sqrt(5 - sqrt 10), +sqrt(5 + sqrt 10), -sqrt(5 + sqrt 10))
+ * times sqrt(R T_ref). */
+size_t dvbm_state_bytes(const dvbm_ctx* ctx);
+
+/* Copy the current state out / in (checkpoint / resume).  bytes must equal
+ * dvbm_state_bytes.  set_state refills the ghost layers. */
+dvbm_status dvbm_get_state(dvbm_ctx* ctx, void* buf, size_t bytes, int on_device);
+dvbm_status dvbm_set_state(dvbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
+
+/* Time step size fixed at dvbm_init (0 before). */
+double dvbm_dt(const dvbm_ctx* ctx);
+
+/* Number of steps taken since dvbm_init / dvbm_set_state. */
+long long dvbm_steps_taken(const dvbm_ctx* ctx);
+
+/* Last error message of ctx (or of the last failed dvbm_create if ctx is
+ * NULL).  Valid until the next call on that context. */
+const char* dvbm_last_error(const dvbm_ctx* ctx);
+
+/* Release the context and its device buffers (NULL is a no-op). */
+void dvbm_destroy(dvbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVBM_H */

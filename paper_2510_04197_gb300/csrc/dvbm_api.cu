@@ -1,0 +1,385 @@
+// dvbm_api.cu -- the C ABI declared in include/dvbm.h.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/dvbm.h"
+#include "dvbm_internal.h"
+
+using namespace dvbm;
+
+struct dvbm_ctx {
+  int Nx = 0, Ny = 0, storage = 0;
+  double Pr = 0, gamma = 0, mu = 0;
+  dvbm_opts opts{};
+  dvbm_bc bcs[4]{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  Geom G{};
+  Phys P{};
+  Macro M{};
+  BCDev bc{};
+  bool any_ghost_kernel = true;
+  size_t elem = 8;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  unsigned int* flag = nullptr;
+  double* partial = nullptr;
+  int nred = 0;
+  double dt = 0.0;
+  long long steps = 0;
+  bool initialised = false;
+  std::string err;
+};
+
+static std::string g_create_error;
+
+static dvbm_status fail(dvbm_ctx* c, dvbm_status s, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (c) c->err = msg; else g_create_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                   \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? DVBM_ENOMEM : DVBM_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                             \
+  } while (0)
+
+extern "C" dvbm_status dvbm_default_opts(dvbm_opts* o) {
+  if (!o) return DVBM_EINVAL;
+  o->Lx = 1.0;
+  o->Ly = 0.0;
+  o->R = 1.0;
+  o->T_ref = 1.0;
+  o->rho0 = 1.0;
+  o->T0 = 1.0;
+  o->beta = 1.2;
+  o->cfl = 0.01;
+  o->dt = 0.0;
+  o->check_every = 0;
+  o->timeout_s = 600.0;
+  return DVBM_OK;
+}
+
+static void set_step_factors(dvbm_ctx* c) {
+  const double dx = c->opts.Lx / c->Nx, dy = c->opts.Ly / c->Ny;
+  for (int k = 0; k < 5; ++k) {
+    c->P.kxv[k] = c->dt / dx * c->M.c * xi_of(k);
+    c->P.kyv[k] = c->dt / dy * c->M.c * xi_of(k);
+    c->P.kxvf[k] = (float)c->P.kxv[k];
+    c->P.kyvf[k] = (float)c->P.kyv[k];
+  }
+  c->P.dt = c->dt;
+}
+
+extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, double Pr, double gamma,
+                                   double mu, const dvbm_bc bcs[4], int storage, const dvbm_opts* opts,
+                                   void* stream) {
+  if (!out) return fail(nullptr, DVBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (lattice != DVBM_D2Q25_SPLIT_II) return fail(nullptr, DVBM_EINVAL, "unsupported lattice %d", lattice);
+  if (storage != DVBM_FP64 && storage != DVBM_FP32DEV) return fail(nullptr, DVBM_EINVAL, "bad storage %d", storage);
+  if (Nx < 4 || Ny < 4 || Nx > (1 << 20) || Ny > 65535 || (long long)Nx * Ny > (1ll << 31))
+    return fail(nullptr, DVBM_EINVAL, "grid %d x %d out of range (4 <= N, Ny <= 65535)", Nx, Ny);
+  if (!(Pr > 0) || !std::isfinite(Pr)) return fail(nullptr, DVBM_EINVAL, "Pr must be > 0");
+  if (!(gamma > 1.0) || !(gamma <= 2.0)) return fail(nullptr, DVBM_EINVAL, "gamma must be in (1, 2] for split II");
+  if (!(mu > 0) || !std::isfinite(mu)) return fail(nullptr, DVBM_EINVAL, "mu must be > 0");
+  dvbm_opts o;
+  dvbm_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.Lx > 0)) return fail(nullptr, DVBM_EINVAL, "Lx must be > 0");
+  if (!(o.Ly > 0)) o.Ly = o.Lx * Ny / Nx;
+  if (!(o.R > 0) || !(o.T_ref > 0) || !(o.rho0 > 0) || !(o.T0 > 0))
+    return fail(nullptr, DVBM_EINVAL, "R, T_ref, rho0, T0 must be > 0");
+  if (!(o.beta >= 1.0 && o.beta <= 2.0)) return fail(nullptr, DVBM_EINVAL, "beta must be in [1, 2]");
+  if (!(o.cfl > 0) && !(o.dt > 0)) return fail(nullptr, DVBM_EINVAL, "need cfl > 0 or dt > 0");
+  if (!(o.timeout_s > 0)) o.timeout_s = 600.0;
+  dvbm_bc b[4];
+  for (int s = 0; s < 4; ++s) {
+    if (bcs) b[s] = bcs[s];
+    else { b[s].kind = DVBM_BC_PERIODIC; b[s].u_wall[0] = b[s].u_wall[1] = 0; b[s].T_wall = 1; }
+    if (b[s].kind < 0 || b[s].kind > 2) return fail(nullptr, DVBM_EINVAL, "bad boundary kind on side %d", s);
+    if (b[s].kind == DVBM_BC_WALL && !(b[s].T_wall > 0)) return fail(nullptr, DVBM_EINVAL, "wall T must be > 0");
+  }
+  for (int a = 0; a < 2; ++a)
+    if ((b[2 * a].kind == DVBM_BC_PERIODIC) != (b[2 * a + 1].kind == DVBM_BC_PERIODIC))
+      return fail(nullptr, DVBM_EINVAL, "periodic boundaries must be paired on axis %d", a);
+
+  dvbm_ctx* c = new dvbm_ctx();
+  c->Nx = Nx; c->Ny = Ny; c->storage = storage;
+  c->Pr = Pr; c->gamma = gamma; c->mu = mu;
+  c->opts = o;
+  for (int s = 0; s < 4; ++s) c->bcs[s] = b[s];
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  c->elem = storage == DVBM_FP64 ? 8 : 4;
+  const int align = 128 / (int)c->elem;  // elements per 128 B
+  c->G.Nx = Nx; c->G.Ny = Ny;
+  c->G.xoff = align;
+  c->G.pitch = ((Nx + align + 2 + align - 1) / align) * align;
+  c->G.plane = (long long)(Ny + 4) * c->G.pitch;
+  const double c2 = o.R * o.T_ref;
+  c->M.c = std::sqrt(c2); c->M.T_ref = o.T_ref; c->M.R = o.R; c->M.gamma = gamma;
+  c->P.c2 = c2; c->P.inv_c2 = 1.0 / c2;
+  c->P.gm1 = gamma - 1.0;
+  c->P.epsf = 1.0 / (gamma - 1.0) - 1.0;
+  c->P.mu = mu; c->P.Pr = Pr;
+  c->P.prc = Pr < 1.0 ? -1 : (Pr > 1.0 ? 1 : 0);
+  c->P.hb = 0.5 * o.beta;
+  c->P.fref0 = o.rho0;
+  c->P.gref0 = o.rho0 * (o.R / (gamma - 1.0) - o.R) * o.T0;
+  for (int s = 0; s < 4; ++s) {
+    c->bc.kind[s] = b[s].kind;
+    c->bc.uw[s][0] = b[s].u_wall[0]; c->bc.uw[s][1] = b[s].u_wall[1];
+    c->bc.Tw[s] = b[s].T_wall;
+  }
+  const size_t bytes = (size_t)NPOP * c->G.plane * c->elem;
+  for (int k = 0; k < 2; ++k) {
+    cudaError_t e = cudaMalloc(&c->buf[k], bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      dvbm_destroy(c);
+      return fail(nullptr, DVBM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  c->nred = 4 * 152;
+  if (cudaMalloc(&c->flag, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&c->partial, sizeof(double) * 6 * c->nred) != cudaSuccess) {
+    cudaGetLastError();
+    dvbm_destroy(c);
+    return fail(nullptr, DVBM_ENOMEM, "cudaMalloc of work buffers failed");
+  }
+  if (cudaMemsetAsync(c->buf[0], 0, bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->buf[1], 0, bytes, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->flag, 0, sizeof(unsigned int), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    dvbm_destroy(c);
+    return fail(nullptr, DVBM_ECUDA, "buffer initialisation failed");
+  }
+  *out = c;
+  return DVBM_OK;
+}
+
+// stream-ordered wait with a host-side time limit
+static dvbm_status wait_stream(dvbm_ctx* c) {
+  cudaEvent_t ev;
+  CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, c->stream);
+  if (e != cudaSuccess) { cudaEventDestroy(ev); return fail(c, DVBM_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e)); }
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return fail(c, DVBM_ECUDA, "stream error: %s", cudaGetErrorString(e)); }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > c->opts.timeout_s) { cudaEventDestroy(ev); return fail(c, DVBM_ETIMEOUT, "stream did not finish within %.1f s", c->opts.timeout_s); }
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  return DVBM_OK;
+}
+
+static dvbm_status check_flag(dvbm_ctx* c) {
+  unsigned int h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->flag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  dvbm_status s = wait_stream(c);
+  if (s != DVBM_OK) return s;
+  if (h) return fail(c, DVBM_EUNSTABLE, "a cell reached rho <= 0, T <= 0 or a non-finite value (after %lld steps)", c->steps);
+  return DVBM_OK;
+}
+
+static dvbm_status fill_ghosts(dvbm_ctx* c, void* b) {
+  CUDA_TRY(c, launch_ghost(c->storage, b, c->G, c->P, c->M, c->bc, c->stream));
+  return DVBM_OK;
+}
+
+// device copies of host field arrays (or pass-through for device pointers)
+struct DevFields {
+  const double* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* owned = nullptr;
+  ~DevFields() { if (owned) cudaFree(owned); }
+};
+
+static dvbm_status stage_fields(dvbm_ctx* c, DevFields& F, const double* const in[4], int on_device) {
+  const size_t n = (size_t)c->Nx * c->Ny;
+  for (int k = 0; k < 4; ++k)
+    if (!in[k]) return fail(c, DVBM_EINVAL, "field pointer %d is NULL", k);
+  if (on_device) {
+    for (int k = 0; k < 4; ++k) F.p[k] = in[k];
+    return DVBM_OK;
+  }
+  CUDA_TRY(c, cudaMalloc(&F.owned, 4 * n * sizeof(double)));
+  for (int k = 0; k < 4; ++k) {
+    CUDA_TRY(c, cudaMemcpyAsync(F.owned + k * n, in[k], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    F.p[k] = F.owned + k * n;
+  }
+  return DVBM_OK;
+}
+
+extern "C" dvbm_status dvbm_init(dvbm_ctx* c, const double* rho, const double* ux, const double* uy,
+                                 const double* T, int on_device) {
+  if (!c) return DVBM_EINVAL;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const double* in[4] = {rho, ux, uy, T};
+  DevFields F;
+  dvbm_status s = stage_fields(c, F, in, on_device);
+  if (s != DVBM_OK) return s;
+  const long long n = (long long)c->Nx * c->Ny;
+  CUDA_TRY(c, launch_speed(F.p[0], F.p[1], F.p[2], F.p[3], n, c->partial, c->nred, c->M, c->stream));
+  std::vector<double> h(2 * c->nred);
+  CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  s = wait_stream(c);
+  if (s != DVBM_OK) return s;
+  double vmax = 0.0, bad = 0.0;
+  for (int b = 0; b < c->nred; ++b) { vmax = std::fmax(vmax, h[2 * b]); bad += h[2 * b + 1]; }
+  if (bad > 0) return fail(c, DVBM_EINVAL, "%.0f cells with rho <= 0, T <= 0 or non-finite values", bad);
+  if (c->opts.dt > 0) c->dt = c->opts.dt;
+  else c->dt = c->opts.cfl * std::fmin(c->opts.Lx / c->Nx, c->opts.Ly / c->Ny) / vmax;
+  set_step_factors(c);
+  c->cur = 0;
+  CUDA_TRY(c, launch_init(c->storage, c->buf[0], F.p[0], F.p[1], F.p[2], F.p[3], c->G, c->P, c->M, c->stream));
+  s = fill_ghosts(c, c->buf[0]);
+  if (s != DVBM_OK) return s;
+  CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(unsigned int), c->stream));
+  s = wait_stream(c);  // the staged host copies are freed on return
+  if (s != DVBM_OK) return s;
+  c->steps = 0;
+  c->initialised = true;
+  return DVBM_OK;
+}
+
+extern "C" dvbm_status dvbm_step(dvbm_ctx* c, int n) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->initialised) return fail(c, DVBM_ESTATE, "dvbm_step before dvbm_init / dvbm_set_state");
+  if (n < 0) return fail(c, DVBM_EINVAL, "n must be >= 0");
+  const int every = c->opts.check_every;
+  for (int i = 0; i < n; ++i) {
+    void* src = c->buf[c->cur];
+    void* dst = c->buf[1 - c->cur];
+    CUDA_TRY(c, launch_step(c->storage, src, dst, c->G, c->P, c->flag, c->stream));
+    dvbm_status s = fill_ghosts(c, dst);
+    if (s != DVBM_OK) return s;
+    c->cur = 1 - c->cur;
+    ++c->steps;
+    if (every > 0 && (i + 1) % every == 0) {
+      s = check_flag(c);
+      if (s != DVBM_OK) return s;
+    }
+  }
+  if (every == 0 && n > 0) return check_flag(c);
+  return DVBM_OK;
+}
+
+extern "C" dvbm_status dvbm_moments(dvbm_ctx* c, double* rho, double* ux, double* uy, double* T, int on_device) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
+  const size_t n = (size_t)c->Nx * c->Ny;
+  double* outs[4] = {rho, ux, uy, T};
+  if (on_device) {
+    CUDA_TRY(c, launch_moments(c->storage, c->buf[c->cur], rho, ux, uy, T, c->G, c->P, c->M, c->stream));
+    return DVBM_OK;
+  }
+  double* tmp = nullptr;
+  CUDA_TRY(c, cudaMalloc(&tmp, 4 * n * sizeof(double)));
+  cudaError_t e = launch_moments(c->storage, c->buf[c->cur], tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, c->G, c->P,
+                                 c->M, c->stream);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    if (outs[k]) e = cudaMemcpyAsync(outs[k], tmp + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  dvbm_status s = e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "moments: %s", cudaGetErrorString(e));
+  cudaFree(tmp);
+  return s;
+}
+
+extern "C" dvbm_status dvbm_totals(dvbm_ctx* c, double out[4]) {
+  if (!c || !out) return DVBM_EINVAL;
+  if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
+  CUDA_TRY(c, launch_totals(c->storage, c->buf[c->cur], c->partial, c->nred, c->G, c->P, c->M, c->stream));
+  std::vector<double> h(6 * c->nred);
+  CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  dvbm_status s = wait_stream(c);
+  if (s != DVBM_OK) return s;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < c->nred; ++b)
+    for (int k = 0; k < 5; ++k) acc[k] += h[6 * b + k];
+  const double dV = (c->opts.Lx / c->Nx) * (c->opts.Ly / c->Ny);
+  for (int k = 0; k < 4; ++k) out[k] = acc[k] * dV;
+  if (acc[4] > 0) return fail(c, DVBM_EUNSTABLE, "%.0f cells with rho <= 0, T <= 0 or non-finite values", acc[4]);
+  return DVBM_OK;
+}
+
+extern "C" size_t dvbm_state_bytes(const dvbm_ctx* c) {
+  if (!c) return 0;
+  return (size_t)NPOP * c->Nx * c->Ny * c->elem + 8;
+}
+
+extern "C" dvbm_status dvbm_get_state(dvbm_ctx* c, void* buf, size_t bytes, int on_device) {
+  if (!c || !buf) return DVBM_EINVAL;
+  if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
+  if (bytes != dvbm_state_bytes(c)) return fail(c, DVBM_EINVAL, "state buffer must be %zu bytes", dvbm_state_bytes(c));
+  const size_t pb = bytes - 8;
+  void* dev = buf;
+  if (!on_device) CUDA_TRY(c, cudaMalloc(&dev, pb));
+  cudaError_t e = launch_pack(c->storage, c->buf[c->cur], dev, 1, c->G, c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(buf, dev, pb, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((char*)buf + pb, &c->steps, 8, on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                        c->stream);
+  dvbm_status s = e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "get_state: %s", cudaGetErrorString(e));
+  if (!on_device) cudaFree(dev);
+  return s;
+}
+
+extern "C" dvbm_status dvbm_set_state(dvbm_ctx* c, const void* buf, size_t bytes, int on_device) {
+  if (!c || !buf) return DVBM_EINVAL;
+  if (bytes != dvbm_state_bytes(c)) return fail(c, DVBM_EINVAL, "state buffer must be %zu bytes", dvbm_state_bytes(c));
+  if (!(c->dt > 0)) {
+    if (!(c->opts.dt > 0)) return fail(c, DVBM_ESTATE, "set_state needs dt: call dvbm_init first or set opts.dt");
+    c->dt = c->opts.dt;
+    set_step_factors(c);
+  }
+  const size_t pb = bytes - 8;
+  void* dev = (void*)buf;
+  if (!on_device) {
+    CUDA_TRY(c, cudaMalloc(&dev, pb));
+  }
+  cudaError_t e = cudaSuccess;
+  if (!on_device) e = cudaMemcpyAsync(dev, buf, pb, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_pack(c->storage, c->buf[c->cur], dev, 0, c->G, c->stream);
+  long long st = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st, (const char*)buf + pb, 8, on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                        c->stream);
+  dvbm_status s = e == cudaSuccess ? fill_ghosts(c, c->buf[c->cur]) : fail(c, DVBM_ECUDA, "set_state: %s", cudaGetErrorString(e));
+  if (s == DVBM_OK) s = wait_stream(c);
+  if (!on_device) cudaFree(dev);
+  if (s != DVBM_OK) return s;
+  c->steps = st;
+  c->initialised = true;
+  return DVBM_OK;
+}
+
+extern "C" double dvbm_dt(const dvbm_ctx* c) { return c ? c->dt : 0.0; }
+extern "C" long long dvbm_steps_taken(const dvbm_ctx* c) { return c ? c->steps : 0; }
+extern "C" const char* dvbm_last_error(const dvbm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+extern "C" void dvbm_destroy(dvbm_ctx* c) {
+  if (!c) return;
+  if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < 2; ++k) if (c->buf[k]) cudaFree(c->buf[k]);
+  if (c->flag) cudaFree(c->flag);
+  if (c->partial) cudaFree(c->partial);
+  delete c;
+}

@@ -1,0 +1,346 @@
+// dvbm_device.cuh -- device-side building blocks of the GB300 DVBM step.
+//
+// Model: double-distribution quasi-equilibrium BGK on the D2Q25 Gauss--Hermite
+// lattice, internal non-translational energy split (II).  Everything here is
+// written in units of c = sqrt(R T_ref): xi = v / c, theta = T / T_ref,
+// Hermite coefficients A_ab = a_{x^a y^b} / c^(a+b), so that the Grad
+// expansion (Sec. II.D.2, Eq. Grad_g; App. D) factorises into 1-D
+// probabilists' Hermite polynomials:
+//     F_pq = W_p W_q sum_{a+b<=N} A_ab He_a(xi_p) He_b(xi_q) / (a! b!).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dvbm {
+
+// ---- D2Q25 lattice (App. G): 1-D nodes are the roots of He_5 ---------------
+// node k: 0, +sqrt(5 - sqrt 10), -sqrt(5 - sqrt 10), +sqrt(5 + sqrt 10), -sqrt(5 + sqrt 10)
+constexpr double XA = 1.3556261799742659;   // sqrt(5 - sqrt(10))
+constexpr double XB = 2.8569700138728056;   // sqrt(5 + sqrt(10))
+// 1-D Gauss--Hermite weights: 8/15 and (7 +- 2 sqrt 10)/60
+constexpr double W0 = 0.53333333333333333;  // 8/15
+constexpr double WA = 0.22207592200561264;  // (7 + 2 sqrt(10)) / 60
+constexpr double WB = 0.011257411327720689; // (7 - 2 sqrt(10)) / 60
+
+constexpr int Q = 25;
+constexpr int NPOP = 50;  // f (0..24) and g (25..49); population c = 5 p + q
+
+__host__ __device__ constexpr double xi_of(int k) {
+  return k == 0 ? 0.0 : k == 1 ? XA : k == 2 ? -XA : k == 3 ? XB : -XB;
+}
+__host__ __device__ constexpr double w_of(int k) {
+  return k == 0 ? W0 : (k <= 2 ? WA : WB);
+}
+__host__ __device__ constexpr int sgn_of(int k) { return k == 0 ? 0 : (k == 1 || k == 3) ? 1 : -1; }
+// probabilists' Hermite polynomials He_n(x), n <= 4
+__host__ __device__ constexpr double he(int n, double x) {
+  return n == 0 ? 1.0 : n == 1 ? x : n == 2 ? x * x - 1.0 : n == 3 ? x * x * x - 3.0 * x
+                                                                      : x * x * x * x - 6.0 * x * x + 3.0;
+}
+__host__ __device__ constexpr double inv_fact(int n) {
+  return n == 0 ? 1.0 : n == 1 ? 1.0 : n == 2 ? 0.5 : n == 3 ? 1.0 / 6.0 : 1.0 / 24.0;
+}
+// W_k He_n(xi_k) / n!
+__host__ __device__ constexpr double kh(int k, int n) { return w_of(k) * he(n, xi_of(k)) * inv_fact(n); }
+
+// ---- launch-invariant parameters (passed by value, constant bank) ---------
+struct Geom {
+  int Nx, Ny;
+  int pitch;             // elements per row (ghost columns included)
+  int xoff;              // element offset of x = 0 inside a row
+  long long plane;       // elements per population plane = (Ny + 4) * pitch
+};
+
+struct Phys {
+  double c2, inv_c2;     // R T_ref and 1 / (R T_ref)
+  double gm1;            // gamma - 1 = R / C_v
+  double epsf;           // C_v/R - D/2 = (2 - gamma)/(gamma - 1): eps/(R T) of split II
+  double dt, mu, Pr;
+  int prc;               // -1: Pr < 1, 0: Pr == 1, +1: Pr > 1
+  double hb;             // beta / 2
+  double kxv[5], kyv[5]; // dt/dx * c * xi_k and dt/dy * c * xi_k
+  float kxvf[5], kyvf[5];
+  double fref0, gref0;   // FP32DEV reference: f_ref = w rho0, g_ref = w rho0 (C_v - R) T0
+  double rho_ref_mom;    // unused padding for alignment
+};
+
+__device__ __forceinline__ long long cell_index(const Geom& G, int y, int x) {
+  return (long long)(y + 2) * G.pitch + x + G.xoff;
+}
+
+// ---- macroscopic state and collision coefficients -------------------------
+// Raw dimensionless moments of f (mu_ab = sum_i xi_x^a xi_y^b f_i, a + b <= 3)
+// and of g (physical units: G00 = sum g, G10/G01 = sum xi g).
+struct Moments {
+  double m00, m10, m01, m20, m11, m02, m30, m21, m12, m03;
+  double g00, g10, g01;
+};
+
+// Combined expansion coefficients of one collision:
+//   F_new = a1 F + W W sum C_ab He He/(a! b!) - advection,
+// with C = (dt/tau1) A^eq + (dt/tau1 - dt/tau2) (A* - A^eq), which equals
+// F - (dt/tau1)(F - F*) - (dt/tau2)(F* - F^eq) by linearity of the expansion.
+struct Coeffs {
+  double f00, f10, f01, f20, f11, f02, f30, f21, f12, f03, f40, f31, f22, f13, f04;
+  double g00, g10, g01, g20, g11, g02;  // physical units of g
+  double a1;                            // 1 - dt/tau1
+  double k1;                            // dt/tau1
+  bool bad;                             // rho <= 0, theta <= 0 or not finite
+};
+
+// Equilibrium coefficients of f (App. D theta-form) for rho, u (in units of
+// c) and s = theta - 1, via the 1-D Hermite recurrences
+//   A_{n+1} = u A_n + n s A_{n-1} along each axis.
+struct EqF { double a00, a10, a01, a20, a11, a02, a30, a21, a12, a03, a40, a31, a22, a13, a04; };
+
+__device__ __forceinline__ EqF eq_f(double rho, double ux, double uy, double s) {
+  EqF e;
+  double rs = rho * s;
+  e.a00 = rho;
+  e.a10 = rho * ux;
+  e.a01 = rho * uy;
+  e.a20 = fma(e.a10, ux, rs);
+  e.a11 = e.a10 * uy;
+  e.a02 = fma(e.a01, uy, rs);
+  e.a30 = fma(e.a20, ux, 2.0 * s * e.a10);
+  e.a03 = fma(e.a02, uy, 2.0 * s * e.a01);
+  e.a21 = e.a20 * uy;
+  e.a12 = e.a02 * ux;
+  e.a40 = fma(e.a30, ux, 3.0 * s * e.a20);
+  e.a04 = fma(e.a03, uy, 3.0 * s * e.a02);
+  e.a31 = e.a30 * uy;
+  e.a13 = e.a03 * ux;
+  e.a22 = e.a20 * fma(uy, uy, s);
+  return e;
+}
+
+// Collision coefficients from the moments (Sec. II.C relaxation times,
+// Table I split-II quasi-equilibria).  PRC selects the Prandtl case at
+// compile time: -1 (Pr < 1), 0 (Pr = 1), +1 (Pr > 1).
+//   Pr < 1: A*_3 = H_3(f) - S(u, Delta); A*_g1 = sum xi g; else equilibrium.
+//   Pr > 1: A*_2 = A^eq_2 + Delta', A*_3 = A^eq_3 + S(u, Delta'),
+//           A*_4 = A^eq_4 - [Delta' delta]_cyc; g* = g^eq,
+// with Delta = H_2(f) - A^eq_2, Delta' its traceless part and
+// S(u, A)_abc = [u_a A_bc]_cyc - tr(A)/(D+2) [u_a d_bc]_cyc, the symmetric
+// tensor whose contraction is the heat-flux constraint 2 (A u)_a.
+template <int PRC>
+__device__ __forceinline__ Coeffs collision_coeffs(const Moments& m, const Phys& P) {
+  Coeffs C;
+  const double rho = m.m00;
+  const double irho = 1.0 / rho;
+  const double ux = m.m10 * irho, uy = m.m01 * irho;
+  const double Et = fma(0.5, m.m20 + m.m02, m.g00 * P.inv_c2);        // E / c^2
+  const double theta = P.gm1 * fma(-0.5, fma(ux, ux, uy * uy), Et * irho);
+  const double s = theta - 1.0;
+  C.bad = !(rho > 0.0) || !(theta > 0.0) || !(fabs(Et) < 1e300);
+  const double p = rho * P.c2 * theta;                                   // rho R T
+  double k1, k2;                                                         // dt/tau1, dt/tau2
+  if (PRC <= 0) { k1 = P.dt * p / P.mu; k2 = k1 * P.Pr; }
+  else          { k2 = P.dt * p / P.mu; k1 = k2 * P.Pr; }
+  const double s1 = k1 - k2;
+  C.a1 = 1.0 - k1;
+  C.k1 = k1;
+  EqF e = eq_f(rho, ux, uy, s);
+  // deviations dA = A* - A^eq (zero where Table I keeps equilibrium moments)
+  double d20 = 0, d11 = 0, d02 = 0, d30 = 0, d21 = 0, d12 = 0, d03 = 0;
+  double d40 = 0, d31 = 0, d13 = 0, d04 = 0, dg10 = 0, dg01 = 0;
+  const double reps = rho * P.epsf * theta;                               // rho eps / c^2
+  if (PRC != 0) {
+    // Delta = H_2(f) - A^eq_2 with H_20 = mu_20 - rho, H_11 = mu_11, H_02 = mu_02 - rho
+    const double Dxx = (m.m20 - rho) - e.a20;
+    const double Dxy = m.m11 - e.a11;
+    const double Dyy = (m.m02 - rho) - e.a02;
+    if (PRC < 0) {
+      const double kap = 0.25 * (Dxx + Dyy);                            // tr(Delta)/(D+2)
+      const double Px = Dxx - kap, Py = Dyy - kap;
+      // H_3(f): mu_30 - 3 mu_10, mu_21 - mu_01, mu_12 - mu_10, mu_03 - 3 mu_01
+      d30 = (fma(-3.0, m.m10, m.m30) - e.a30) - 3.0 * ux * Px;
+      d21 = ((m.m21 - m.m01) - e.a21) - fma(2.0 * ux, Dxy, uy * Px);
+      d12 = ((m.m12 - m.m10) - e.a12) - fma(2.0 * uy, Dxy, ux * Py);
+      d03 = (fma(-3.0, m.m01, m.m03) - e.a03) - 3.0 * uy * Py;
+      // g*: first moment of g (in units of c^2), minus its equilibrium value
+      dg10 = m.g10 * P.inv_c2 - reps * ux;
+      dg01 = m.g01 * P.inv_c2 - reps * uy;
+    } else {
+      const double Tx = 0.5 * (Dxx - Dyy);                              // Delta'_xx = -Delta'_yy
+      d20 = Tx; d11 = Dxy; d02 = -Tx;
+      d30 = 3.0 * ux * Tx;
+      d21 = fma(uy, Tx, 2.0 * ux * Dxy);
+      d12 = fma(-ux, Tx, 2.0 * uy * Dxy);
+      d03 = -3.0 * uy * Tx;
+      d40 = -6.0 * Tx; d31 = -3.0 * Dxy; d13 = -3.0 * Dxy; d04 = 6.0 * Tx;
+    }
+  }
+  C.f00 = k1 * e.a00;
+  C.f10 = k1 * e.a10;
+  C.f01 = k1 * e.a01;
+  C.f20 = fma(s1, d20, k1 * e.a20);
+  C.f11 = fma(s1, d11, k1 * e.a11);
+  C.f02 = fma(s1, d02, k1 * e.a02);
+  C.f30 = fma(s1, d30, k1 * e.a30);
+  C.f21 = fma(s1, d21, k1 * e.a21);
+  C.f12 = fma(s1, d12, k1 * e.a12);
+  C.f03 = fma(s1, d03, k1 * e.a03);
+  C.f40 = fma(s1, d40, k1 * e.a40);
+  C.f31 = fma(s1, d31, k1 * e.a31);
+  C.f22 = k1 * e.a22;
+  C.f13 = fma(s1, d13, k1 * e.a13);
+  C.f04 = fma(s1, d04, k1 * e.a04);
+  // g^eq (split II): A00 = rho eps, A10 = rho eps ux, A20 = rho eps (ux^2 + s) ...
+  // (units of c^2; multiplied back by c^2 for physical g)
+  const double kg = k1 * P.c2;
+  const double sg = s1 * P.c2;
+  C.g00 = kg * reps;
+  C.g10 = fma(sg, dg10, kg * reps * ux);
+  C.g01 = fma(sg, dg01, kg * reps * uy);
+  C.g20 = kg * reps * fma(ux, ux, s);
+  C.g11 = kg * reps * ux * uy;
+  C.g02 = kg * reps * fma(uy, uy, s);
+  return C;
+}
+
+// Pure equilibrium coefficients (for initial conditions and wall ghosts):
+// same layout as Coeffs with C = A^eq, physical g.
+__device__ __forceinline__ Coeffs equilibrium_coeffs(double rho, double ux, double uy, double theta,
+                                                     const Phys& P) {
+  Coeffs C;
+  const double s = theta - 1.0;
+  EqF e = eq_f(rho, ux, uy, s);
+  C.f00 = e.a00; C.f10 = e.a10; C.f01 = e.a01; C.f20 = e.a20; C.f11 = e.a11; C.f02 = e.a02;
+  C.f30 = e.a30; C.f21 = e.a21; C.f12 = e.a12; C.f03 = e.a03;
+  C.f40 = e.a40; C.f31 = e.a31; C.f22 = e.a22; C.f13 = e.a13; C.f04 = e.a04;
+  const double reps = rho * P.epsf * theta * P.c2;
+  C.g00 = reps; C.g10 = reps * ux; C.g01 = reps * uy;
+  C.g20 = reps * fma(ux, ux, s); C.g11 = reps * ux * uy; C.g02 = reps * fma(uy, uy, s);
+  C.a1 = 0.0; C.k1 = 1.0; C.bad = false;
+  return C;
+}
+
+// Macroscopic values (rho, u in physical units, T) from moments.
+__device__ __forceinline__ void macro_from_moments(const Moments& m, const Phys& P, double c, double T_ref,
+                                                   double& rho, double& ux, double& uy, double& T) {
+  rho = m.m00;
+  const double irho = 1.0 / rho;
+  const double uxd = m.m10 * irho, uyd = m.m01 * irho;
+  const double Et = fma(0.5, m.m20 + m.m02, m.g00 * P.inv_c2);
+  const double theta = P.gm1 * fma(-0.5, fma(uxd, uxd, uyd * uyd), Et * irho);
+  ux = uxd * c;
+  uy = uyd * c;
+  T = theta * T_ref;
+}
+
+// ---- sum-factorised moment accumulation -----------------------------------
+// Accumulate the contribution of the five populations (p, q = 0..4) of one
+// x-node p.  f[q] and g[q] are the values (double).
+template <int p>
+__device__ __forceinline__ void accumulate_moments(Moments& m, const double (&f)[5], const double (&g)[5]) {
+  const double sA = f[1] + f[2], dA = f[1] - f[2], sB = f[3] + f[4], dB = f[3] - f[4];
+  const double m0 = f[0] + sA + sB;
+  const double m1 = fma(XA, dA, XB * dB);
+  const double m2 = fma(XA * XA, sA, (XB * XB) * sB);
+  const double m3 = fma(XA * XA * XA, dA, (XB * XB * XB) * dB);
+  const double n0 = g[0] + (g[1] + g[2]) + (g[3] + g[4]);
+  const double n1 = fma(XA, g[1] - g[2], XB * (g[3] - g[4]));
+  m.m00 += m0; m.m01 += m1; m.m02 += m2; m.m03 += m3;
+  m.g00 += n0; m.g01 += n1;
+  if (p != 0) {
+    constexpr double x = xi_of(p);
+    m.m10 = fma(x, m0, m.m10);
+    m.m11 = fma(x, m1, m.m11);
+    m.m12 = fma(x, m2, m.m12);
+    m.m20 = fma(x * x, m0, m.m20);
+    m.m21 = fma(x * x, m1, m.m21);
+    m.m30 = fma(x * x * x, m0, m.m30);
+    m.g10 = fma(x, n0, m.g10);
+  }
+}
+
+// ---- sum-factorised Grad expansion ----------------------------------------
+// h^b_p = W_p sum_a C_ab He_a(xi_p)/a!  for the f expansion (N = 4).
+template <int p>
+__device__ __forceinline__ void hf_of(const Coeffs& C, double (&h)[5]) {
+  h[0] = kh(p, 0) * C.f00 + kh(p, 2) * C.f20 + kh(p, 4) * C.f40;
+  h[1] = kh(p, 0) * C.f01 + kh(p, 2) * C.f21;
+  h[2] = kh(p, 0) * C.f02;
+  h[3] = kh(p, 0) * C.f03;
+  h[4] = kh(p, 0) * C.f04;
+  if (p != 0) {
+    h[0] += kh(p, 1) * C.f10 + kh(p, 3) * C.f30;
+    h[1] += kh(p, 1) * C.f11 + kh(p, 3) * C.f31;
+    h[2] += kh(p, 1) * C.f12 + kh(p, 2) * C.f22;
+    h[3] += kh(p, 1) * C.f13;
+  } else {
+    h[2] += kh(p, 2) * C.f22;
+  }
+}
+template <int p>
+__device__ __forceinline__ void hg_of(const Coeffs& C, double (&h)[3]) {
+  h[0] = kh(p, 0) * C.g00 + kh(p, 2) * C.g20;
+  h[1] = kh(p, 0) * C.g01;
+  h[2] = kh(p, 0) * C.g02;
+  if (p != 0) {
+    h[0] += kh(p, 1) * C.g10;
+    h[1] += kh(p, 1) * C.g11;
+  }
+}
+// t_q = W_q sum_b h^b He_b(xi_q)/b! for the five y-nodes, using the +-xi
+// symmetry: even part E and odd part O, t(+xi) = E + O, t(-xi) = E - O.
+__device__ __forceinline__ void expand_q5(const double (&h)[5], double (&t)[5]) {
+  t[0] = kh(0, 0) * h[0] + kh(0, 2) * h[2] + kh(0, 4) * h[4];
+  const double EA = kh(1, 0) * h[0] + kh(1, 2) * h[2] + kh(1, 4) * h[4];
+  const double OA = kh(1, 1) * h[1] + kh(1, 3) * h[3];
+  const double EB = kh(3, 0) * h[0] + kh(3, 2) * h[2] + kh(3, 4) * h[4];
+  const double OB = kh(3, 1) * h[1] + kh(3, 3) * h[3];
+  t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
+}
+__device__ __forceinline__ void expand_q3(const double (&h)[3], double (&t)[5]) {
+  t[0] = kh(0, 0) * h[0] + kh(0, 2) * h[2];
+  const double EA = kh(1, 0) * h[0] + kh(1, 2) * h[2];
+  const double OA = kh(1, 1) * h[1];
+  const double EB = kh(3, 0) * h[0] + kh(3, 2) * h[2];
+  const double OB = kh(3, 1) * h[1];
+  t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
+}
+
+// ---- limited slope of the NND reconstruction (Sec. III.A.2) --------------
+// sigma(a, b) = (b/2) phi(a/b) = 1/2 minmod3(beta a, (a+b)/2, beta b)
+//             = minmod3(hb a, (a+b)/4, hb b),  hb = beta/2,
+// (division-free; 0 if a and b differ in sign; b = 0 gives 0).  The three
+// magnitudes are non-negative doubles, so their minimum is taken exactly on
+// the integer pipe by comparing the bit patterns.
+__device__ __forceinline__ double limited_slope(double a, double b, double hb) {
+  const double x = hb * a, z = hb * b, y = 0.25 * (a + b);
+  const unsigned long long mask = 0x7fffffffffffffffull;
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & mask;
+  const unsigned long long ay = (unsigned long long)__double_as_longlong(y) & mask;
+  const unsigned long long az = (unsigned long long)__double_as_longlong(z) & mask;
+  unsigned long long mn = ax < ay ? ax : ay;
+  mn = mn < az ? mn : az;
+  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+  const unsigned long long sgn = (unsigned long long)ba & ~mask;
+  return __longlong_as_double((long long)(((ba ^ bb) >= 0) ? (mn | sgn) : 0ull));
+}
+__device__ __forceinline__ float limited_slope(float a, float b, float hb) {
+  const float x = hb * a, z = hb * b, y = 0.25f * (a + b);
+  const float mn = fminf(fminf(fabsf(x), fabsf(y)), fabsf(z));
+  return ((__float_as_int(a) ^ __float_as_int(b)) >= 0) ? copysignf(mn, a) : 0.0f;
+}
+
+// Flux difference F_{j+1/2} - F_{j-1/2} of the upwind-limited face values
+// along a stride; SGN = sign of the velocity component (never 0 here).
+//   v > 0: faces f_{j-1} + sigma_{j-1}, f_j + sigma_j
+//   v < 0: faces f_j - sigma_j, f_{j+1} - sigma_{j+1}
+template <int SGN, class T>
+__device__ __forceinline__ T flux_difference(const T* __restrict__ ptr, long long stride, T hb) {
+  if (SGN > 0) {
+    const T fm2 = __ldg(ptr - 2 * stride), fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride);
+    const T Dm = fm1 - fm2, D0 = f0 - fm1, Dp = fp1 - f0;
+    return D0 + limited_slope(D0, Dp, hb) - limited_slope(Dm, D0, hb);
+  } else {
+    const T fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride), fp2 = __ldg(ptr + 2 * stride);
+    const T D0 = f0 - fm1, Dp = fp1 - f0, Dpp = fp2 - fp1;
+    return Dp - limited_slope(Dp, Dpp, hb) + limited_slope(D0, Dp, hb);
+  }
+}
+
+}  // namespace dvbm

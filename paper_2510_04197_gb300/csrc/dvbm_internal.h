@@ -1,0 +1,35 @@
+// dvbm_internal.h -- launch wrappers shared by the translation units of libdvbm.
+#pragma once
+#include <cuda_runtime.h>
+#include "dvbm_device.cuh"
+
+namespace dvbm {
+
+struct BCDev {
+  int kind[4];          // xlo, xhi, ylo, yhi (0 periodic, 1 zero-gradient, 2 wall)
+  double uw[4][2];      // wall velocity
+  double Tw[4];         // wall temperature
+};
+
+struct Macro {          // constants needed to turn moments into physical fields
+  double c, T_ref, R, gamma;
+};
+
+cudaError_t launch_step(int storage, const void* src, void* dst, const Geom& G, const Phys& P,
+                        unsigned int* flag, cudaStream_t st);
+cudaError_t launch_init(int storage, void* dst, const double* rho, const double* ux, const double* uy,
+                        const double* T, const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
+cudaError_t launch_ghost(int storage, void* buf, const Geom& G, const Phys& P, const Macro& M,
+                         const BCDev& bc, cudaStream_t st);
+cudaError_t launch_moments(int storage, const void* src, double* rho, double* ux, double* uy, double* T,
+                           const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
+// per-block partial sums: out[blk*6 + {mass, momx, momy, energy, bad, 0}]
+cudaError_t launch_totals(int storage, const void* src, double* partial, int nblocks, const Geom& G,
+                          const Phys& P, const Macro& M, cudaStream_t st);
+// per-block maxima of |u| + sqrt(gamma R T) and a bad-input count: out[blk*2 + {max, bad}]
+cudaError_t launch_speed(const double* rho, const double* ux, const double* uy, const double* T, long long n,
+                         double* partial, int nblocks, const Macro& M, cudaStream_t st);
+cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G,
+                        cudaStream_t st);
+
+}  // namespace dvbm

@@ -1,0 +1,105 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs.  FP64 storage: per-field relative max-norm error 1e-12;
+FP32-deviation storage: 1e-5 on smooth flows."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dvbm_oracle as O
+from paper_2510_04197_gb300 import inputs as I
+from helpers import field_errors, oracle_run, abi_to_oracle_perm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_2510_04197_gb300 import build, dvbm
+    import os
+    if not os.path.exists(dvbm.LIBPATH):
+        build.build()
+    assert torch.cuda.is_available()
+    return dvbm
+
+
+def gpu_run(D, F, Pr, gamma, mu, nsteps, storage=0, bcs=None, dt=None, cfl=0.01, **kw):
+    Ny, Nx = F.rho.shape
+    opts = dict(Lx=F.Lx, Ly=F.Ly, cfl=cfl, **kw)
+    if dt:
+        opts["dt"] = dt
+    sim = D.Simulation(Nx, Ny, Pr, gamma, mu, bcs=bcs, storage=storage, **opts)
+    sim.init(*(torch.tensor(a) for a in (F.rho, F.ux, F.uy, F.T)))
+    sim.step(nsteps)
+    m = {k: v.cpu().numpy() for k, v in sim.moments().items()}
+    return sim, m
+
+
+def test_config1_wave_decay_fp64_1000_steps(D):
+    """64 x 64 shear + entropy waves over a Ma = 0.1 mean flow, Pr = 0.71,
+    gamma = 1.4, 1000 steps at CFL 0.01: FP64 fields within 1e-12 of the oracle."""
+    F = I.wave_decay(64, 64, Ma=0.1, amp=1e-3)
+    sim, g = gpu_run(D, F, 0.71, 1.4, 0.01, 1000)
+    _, o = oracle_run(F, 0.71, 1.4, 0.01, sim.dt, 1000)
+    e = field_errors(g, o)
+    assert max(e.values()) < 1e-12, e
+
+
+@pytest.mark.parametrize("Pr", [0.5, 1.0, 2.0])
+@pytest.mark.parametrize("shape", [(40, 24), (37, 13)])
+def test_ragged_grids_all_prandtl_cases(D, Pr, shape):
+    """Ragged tiles (Nx, Ny not multiples of the 32 x 8 CTA tile), every
+    Prandtl branch, O(1) non-equilibrium: 100 steps within 1e-12."""
+    Nx, Ny = shape
+    F = I.random_smooth(Nx, Ny, seed=11, amp=0.1, Ma=0.5)
+    sim, g = gpu_run(D, F, Pr, 1.4, 2e-3, 100, dt=2e-4)
+    _, o = oracle_run(F, Pr, 1.4, 2e-3, sim.dt, 100)
+    e = field_errors(g, o)
+    assert max(e.values()) < 1e-12, e
+
+
+def test_populations_match_oracle_after_one_step(D):
+    """Element-wise population parity (ABI order mapped onto the oracle's)."""
+    F = I.random_smooth(33, 18, seed=3, amp=0.1, Ma=0.6)
+    sim, _ = gpu_run(D, F, 0.71, 1.67, 2e-3, 1, dt=2e-4)
+    s, _ = oracle_run(F, 0.71, 1.67, 2e-3, sim.dt, 1)
+    pops = sim.populations().cpu().numpy()
+    perm = abi_to_oracle_perm(s.lat)
+    f = pops[:25][perm]
+    g = pops[25:][perm]
+    assert np.abs(f - s.f.numpy()).max() < 1e-14 * np.abs(s.f.numpy()).max() * 10
+    assert np.abs(g - s.g.numpy()).max() < 1e-14 * np.abs(s.g.numpy()).max() * 10
+
+
+def test_fp32_deviation_storage_smooth_flow(D):
+    """FP32-deviation storage on the config-1 flow: relative L-inf error against
+    the FP64 oracle at most 1e-5 after 1000 steps."""
+    F = I.wave_decay(64, 64, Ma=0.1, amp=1e-3)
+    sim, g = gpu_run(D, F, 0.71, 1.4, 0.01, 1000, storage=1)
+    _, o = oracle_run(F, 0.71, 1.4, 0.01, sim.dt, 1000)
+    e = field_errors(g, o)
+    assert max(e.values()) < 1e-5, e
+
+
+def test_uniform_state_fixed_point_and_conservation(D):
+    F = I.random_smooth(48, 40, seed=5, amp=0.1, Ma=0.5)
+    sim, _ = gpu_run(D, F, 0.71, 1.4, 2e-3, 0, dt=2e-4)
+    t0 = sim.totals()
+    sim.step(200)
+    t1 = sim.totals()
+    for a, b in zip(t0, t1):
+        assert abs(a - b) < 1e-13 * max(1.0, abs(a)), (t0, t1)
+
+
+def test_checkpoint_resume_is_bitwise(D):
+    F = I.random_smooth(40, 24, seed=7, amp=0.1, Ma=0.5)
+    a, _ = gpu_run(D, F, 2.0, 1.4, 2e-3, 20, dt=2e-4)
+    ref = a.populations().clone()
+    b, _ = gpu_run(D, F, 2.0, 1.4, 2e-3, 10, dt=2e-4)
+    st = b.get_state()
+    c, _ = gpu_run(D, F, 2.0, 1.4, 2e-3, 0, dt=2e-4)
+    c.set_state(st)
+    assert c.steps == 10
+    c.step(10)
+    assert torch.equal(c.populations(), ref)

@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 DVBM time step (one JSON line on rank 0).
+
+Workload: periodic 4096 x 4096 random-phase multimode flow (Gaussian shell
+spectrum peaking at |k| = 8, rms Ma 0.3, rms dT 0.05, seed 0), Pr = 0.71,
+gamma = 1.4, mu = 5e-5, D2Q25 split II.  A step is one full time step of the
+hot path (moments, collision, advection, update, ghost layers).  ``value`` is
+whole-job MLUPS of FP64 storage with the state resident in HBM; FP32-deviation
+storage is measured on the same workload in ``fp32dev``.  The state (2 x 6.7 GB)
+is far larger than L2, so no L2 flush is needed between steps.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on host cores.
+Under torchrun each rank runs an independent replica (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"fp64": 2 * 50 * 8, "fp32dev": 2 * 50 * 4}  # read + write all populations
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_FP64_TFLOPS = 1.25  # profiling recipe: GB300 FP64 (FMA = 2 flops)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32dev", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=512, help="oracle sample grid size")
+    return ap.parse_args()
+
+
+def workload_config(N):
+    return {"workload": f"periodic multimode flow {N}x{N}, rms Ma 0.3, seed 0 (throughput sweep)",
+            "grid": [N, N], "lattice": "D2Q25", "energy_split": "II", "Pr": 0.71, "gamma": 1.4, "mu": 5e-5,
+            "cfl": 0.01, "beta": 1.2, "l2": "state 2x50 planes x N^2 (> 129 MB L2): no flush needed",
+            "parallelism": "replicas (one independent grid per GPU)"}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2510_04197_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def profile_traffic(kernel_key):
+    """DRAM bytes per cell of a kernel from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    try:
+        with open(PROFILE_TRAFFIC) as fh:
+            t = json.load(fh)
+        e = t.get(kernel_key)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks/throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(N_sample, steps=8):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    a periodic N_sample^2 multimode field of the same recipe, ``steps`` steps."""
+    import torch
+    from oracle import dvbm_oracle as O
+    from paper_2510_04197_gb300 import inputs
+    F = inputs.multimode(N_sample, seed=0, rms_Ma=0.3)
+    t = lambda a: torch.tensor(a, dtype=torch.float64)
+    P = O.Params(Pr=0.71, gamma=1.4, mu=5e-5)
+    sim = O.Simulation(O.Grid(N_sample, N_sample), P, t(F.rho), t(F.ux), t(F.uy), t(F.T), cfl=0.01)
+    sim.run(1)  # warm-up
+    t0 = time.perf_counter()
+    sim.run(steps)
+    el = time.perf_counter() - t0
+    mlups = N_sample * N_sample * steps / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{N_sample}x{N_sample} periodic multimode (same recipe), {steps} FP64 steps after 1 warm-up, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    N = args.cpu_sample
+    steps = args.steps
+    cb = cpu_baseline(N, steps)
+    line = {"metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": N * N / cb["value"] / 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.size), "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(sim, K, stream):
+    """Time K single steps with CUDA events on the library's stream; returns
+    (total ms, list of per-step ms)."""
+    import torch
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    evs[0].record(stream)
+    for i in range(K):
+        sim.step(1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+    return evs[0].elapsed_time(evs[K]), per
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2510_04197_gb300 import dvbm, inputs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    N = args.size
+    F = inputs.multimode(N, seed=rank, rms_Ma=0.3)
+    fields = [torch.tensor(a) for a in (F.rho, F.ux, F.uy, F.T)]
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = load_peaks()
+    results = {}
+    clocks = None
+    for storage in (["fp64"] if args.no_fp32dev else ["fp64", "fp32dev"]):
+        sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, storage=0 if storage == "fp64" else 1, check_every=-1)
+        sim.init(*fields)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if storage == "fp64" else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize()
+        total_ms, per = timed_steps(sim, args.steps, stream)
+        torch.cuda.synchronize()
+        barrier()
+        if sampler:
+            clocks = sampler.stop()
+        tmax = total_ms
+        if dist:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tmax = float(t.item())
+        mlups = N * N * args.steps * world / (tmax * 1e-3) / 1e6
+        tot = sim.totals()  # also raises if the run went unstable
+        results[storage] = {"mlups": mlups, "ms_per_step": tmax / args.steps,
+                            "kernel_ms": statistics.mean(per), "totals": tot}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+
+    # end-to-end through the public API with host (pinned) buffers:
+    # host fields -> dvbm_init -> K steps -> moments back to host
+    e2e = None
+    if not args.no_e2e:
+        pin = [t.pin_memory() for t in fields]
+        outs = {k: torch.empty((N, N), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy", "T")}
+        sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, storage=0, check_every=-1)
+        sim.init_host(*[p.numpy() for p in pin])
+        sim.step(1)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        sim.init_host(*[p.numpy() for p in pin])
+        sim.step(args.steps)
+        import ctypes
+        st = dvbm.lib().dvbm_moments(sim._h, *[ctypes.c_void_p(outs[k].data_ptr()) for k in ("rho", "ux", "uy", "T")], 0)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        assert st == 0
+        e2e = {"value": N * N * args.steps * world / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 4 * 8 * N * N / args.steps, "d2h_bytes_per_step": 4 * 8 * N * N / args.steps,
+               "note": "init from host fields + K steps + moments to host, per-step bytes = total / K"}
+        sim.close()
+
+    if rank != 0:
+        return
+    r64 = results["fp64"]
+    # dominant kernel: the FP64 step; HBM roofline of its algorithmic bytes
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    ach_gbs = BYTES_PER_CELL["fp64"] * N * N / (r64["kernel_ms"] * 1e-3) / 1e9
+    tr = profile_traffic("k_step_fp64")
+    fp64_ops = tr.get("fp64_flops_per_cell") if tr else None
+    roofline_hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach_gbs / hbm_peak, "traffic": (tr["dram_bytes_per_cell"] * N * N if tr else None),
+                    "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    if fp64_ops:
+        ach_tf = fp64_ops * N * N / (r64["kernel_ms"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": ach_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach_tf / NOMINAL_FP64_TFLOPS, "traffic": roofline_hbm["traffic"],
+                    "what": "FP64 pipe: executed FP64 flops per cell (ncu instruction mix, FMA = 2) / step-kernel time; "
+                            "peak = nominal GB300 FP64 1.25 TFLOP/s"}
+    else:
+        roofline = dict(roofline_hbm)
+    line = {"metric": "MLUPS", "value": r64["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(N),
+            "roofline": roofline, "roofline_hbm": roofline_hbm, "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+            "kernel_ms_per_step": r64["kernel_ms"]}
+    if "fp32dev" in results:
+        r32 = results["fp32dev"]
+        g32 = BYTES_PER_CELL["fp32dev"] * N * N / (r32["kernel_ms"] * 1e-3) / 1e9
+        line["fp32dev"] = {"value": r32["mlups"], "unit": "MLUPS", "ms_per_step": r32["ms_per_step"],
+                           "dtype": "f32 storage / f64 moments+equilibria",
+                           "roofline_hbm": {"bound": "hbm", "achieved": g32, "peak": hbm_peak, "unit": "GB/s",
+                                            "frac": g32 / hbm_peak}}
+    line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

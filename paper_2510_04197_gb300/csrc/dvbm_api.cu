@@ -82,6 +82,7 @@ static void set_step_factors(dvbm_ctx* c) {
     c->P.kyvf[k] = (float)c->P.kyv[k];
   }
   c->P.dt = c->dt;
+  c->P.dt_mu = c->dt / c->mu;
 }
 
 extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, double Pr, double gamma,
@@ -138,6 +139,7 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
   c->P.mu = mu; c->P.Pr = Pr;
   c->P.prc = Pr < 1.0 ? -1 : (Pr > 1.0 ? 1 : 0);
   c->P.hb = 0.5 * o.beta;
+  c->P.hq = (long long)std::llround(std::ldexp(0.5 * o.beta, 62));
   c->P.fref0 = o.rho0;
   c->P.gref0 = o.rho0 * (o.R / (gamma - 1.0) - o.R) * o.T0;
   for (int s = 0; s < 4; ++s) {

@@ -56,8 +56,10 @@ struct Phys {
   double gm1;            // gamma - 1 = R / C_v
   double epsf;           // C_v/R - D/2 = (2 - gamma)/(gamma - 1): eps/(R T) of split II
   double dt, mu, Pr;
+  double dt_mu;          // dt / mu
   int prc;               // -1: Pr < 1, 0: Pr == 1, +1: Pr > 1
   double hb;             // beta / 2
+  long long hq;          // round(beta/2 * 2^62), integer-pipe limiter
   double kxv[5], kyv[5]; // dt/dx * c * xi_k and dt/dy * c * xi_k
   float kxvf[5], kyvf[5];
   double fref0, gref0;   // FP32DEV reference: f_ref = w rho0, g_ref = w rho0 (C_v - R) T0
@@ -135,8 +137,8 @@ __device__ __forceinline__ Coeffs collision_coeffs(const Moments& m, const Phys&
   C.bad = !(rho > 0.0) || !(theta > 0.0) || !(fabs(Et) < 1e300);
   const double p = rho * P.c2 * theta;                                   // rho R T
   double k1, k2;                                                         // dt/tau1, dt/tau2
-  if (PRC <= 0) { k1 = P.dt * p / P.mu; k2 = k1 * P.Pr; }
-  else          { k2 = P.dt * p / P.mu; k1 = k2 * P.Pr; }
+  if (PRC <= 0) { k1 = P.dt_mu * p; k2 = k1 * P.Pr; }
+  else          { k2 = P.dt_mu * p; k1 = k2 * P.Pr; }
   const double s1 = k1 - k2;
   C.a1 = 1.0 - k1;
   C.k1 = k1;
@@ -259,45 +261,45 @@ __device__ __forceinline__ void accumulate_moments(Moments& m, const double (&f)
 // h^b_p = W_p sum_a C_ab He_a(xi_p)/a!  for the f expansion (N = 4).
 template <int p>
 __device__ __forceinline__ void hf_of(const Coeffs& C, double (&h)[5]) {
-  h[0] = kh(p, 0) * C.f00 + kh(p, 2) * C.f20 + kh(p, 4) * C.f40;
-  h[1] = kh(p, 0) * C.f01 + kh(p, 2) * C.f21;
-  h[2] = kh(p, 0) * C.f02;
-  h[3] = kh(p, 0) * C.f03;
-  h[4] = kh(p, 0) * C.f04;
   if (p != 0) {
-    h[0] += kh(p, 1) * C.f10 + kh(p, 3) * C.f30;
-    h[1] += kh(p, 1) * C.f11 + kh(p, 3) * C.f31;
-    h[2] += kh(p, 1) * C.f12 + kh(p, 2) * C.f22;
-    h[3] += kh(p, 1) * C.f13;
-  } else {
-    h[2] += kh(p, 2) * C.f22;
+    h[0] = fma(kh(p, 4), C.f40, fma(kh(p, 3), C.f30, fma(kh(p, 2), C.f20, fma(kh(p, 1), C.f10, kh(p, 0) * C.f00))));
+    h[1] = fma(kh(p, 3), C.f31, fma(kh(p, 2), C.f21, fma(kh(p, 1), C.f11, kh(p, 0) * C.f01)));
+    h[2] = fma(kh(p, 2), C.f22, fma(kh(p, 1), C.f12, kh(p, 0) * C.f02));
+    h[3] = fma(kh(p, 1), C.f13, kh(p, 0) * C.f03);
+  } else {  // He_1(0) = He_3(0) = 0
+    h[0] = fma(kh(p, 4), C.f40, fma(kh(p, 2), C.f20, kh(p, 0) * C.f00));
+    h[1] = fma(kh(p, 2), C.f21, kh(p, 0) * C.f01);
+    h[2] = fma(kh(p, 2), C.f22, kh(p, 0) * C.f02);
+    h[3] = kh(p, 0) * C.f03;
   }
+  h[4] = kh(p, 0) * C.f04;
 }
 template <int p>
 __device__ __forceinline__ void hg_of(const Coeffs& C, double (&h)[3]) {
-  h[0] = kh(p, 0) * C.g00 + kh(p, 2) * C.g20;
-  h[1] = kh(p, 0) * C.g01;
-  h[2] = kh(p, 0) * C.g02;
   if (p != 0) {
-    h[0] += kh(p, 1) * C.g10;
-    h[1] += kh(p, 1) * C.g11;
+    h[0] = fma(kh(p, 2), C.g20, fma(kh(p, 1), C.g10, kh(p, 0) * C.g00));
+    h[1] = fma(kh(p, 1), C.g11, kh(p, 0) * C.g01);
+  } else {
+    h[0] = fma(kh(p, 2), C.g20, kh(p, 0) * C.g00);
+    h[1] = kh(p, 0) * C.g01;
   }
+  h[2] = kh(p, 0) * C.g02;
 }
 // t_q = W_q sum_b h^b He_b(xi_q)/b! for the five y-nodes, using the +-xi
 // symmetry: even part E and odd part O, t(+xi) = E + O, t(-xi) = E - O.
 __device__ __forceinline__ void expand_q5(const double (&h)[5], double (&t)[5]) {
-  t[0] = kh(0, 0) * h[0] + kh(0, 2) * h[2] + kh(0, 4) * h[4];
-  const double EA = kh(1, 0) * h[0] + kh(1, 2) * h[2] + kh(1, 4) * h[4];
-  const double OA = kh(1, 1) * h[1] + kh(1, 3) * h[3];
-  const double EB = kh(3, 0) * h[0] + kh(3, 2) * h[2] + kh(3, 4) * h[4];
-  const double OB = kh(3, 1) * h[1] + kh(3, 3) * h[3];
+  t[0] = fma(kh(0, 4), h[4], fma(kh(0, 2), h[2], kh(0, 0) * h[0]));
+  const double EA = fma(kh(1, 4), h[4], fma(kh(1, 2), h[2], kh(1, 0) * h[0]));
+  const double OA = fma(kh(1, 3), h[3], kh(1, 1) * h[1]);
+  const double EB = fma(kh(3, 4), h[4], fma(kh(3, 2), h[2], kh(3, 0) * h[0]));
+  const double OB = fma(kh(3, 3), h[3], kh(3, 1) * h[1]);
   t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
 }
 __device__ __forceinline__ void expand_q3(const double (&h)[3], double (&t)[5]) {
-  t[0] = kh(0, 0) * h[0] + kh(0, 2) * h[2];
-  const double EA = kh(1, 0) * h[0] + kh(1, 2) * h[2];
+  t[0] = fma(kh(0, 2), h[2], kh(0, 0) * h[0]);
+  const double EA = fma(kh(1, 2), h[2], kh(1, 0) * h[0]);
   const double OA = kh(1, 1) * h[1];
-  const double EB = kh(3, 0) * h[0] + kh(3, 2) * h[2];
+  const double EB = fma(kh(3, 2), h[2], kh(3, 0) * h[0]);
   const double OB = kh(3, 1) * h[1];
   t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
 }
@@ -305,20 +307,21 @@ __device__ __forceinline__ void expand_q3(const double (&h)[3], double (&t)[5]) 
 // ---- limited slope of the NND reconstruction (Sec. III.A.2) --------------
 // sigma(a, b) = (b/2) phi(a/b) = 1/2 minmod3(beta a, (a+b)/2, beta b)
 //             = minmod3(hb a, (a+b)/4, hb b),  hb = beta/2,
-// (division-free; 0 if a and b differ in sign; b = 0 gives 0).  The three
-// magnitudes are non-negative doubles, so their minimum is taken exactly on
-// the integer pipe by comparing the bit patterns.
+// (division-free; 0 if a and b differ in sign; b = 0 gives 0).
+// When a and b share a sign, the three candidates x = hb a, y = (a+b)/4,
+// z = hb b share it too, and for doubles of one sign the signed-int64 order of
+// the raw bit patterns is the order of magnitudes (sign-magnitude encoding).
+// So the minimum-magnitude candidate, sign included, is the signed-int64
+// minimum of the bit patterns: no FP64 compare, abs or min is needed.
+__device__ __forceinline__ double minmod_sel(double a, double b, double x, double y, double z) {
+  const long long bx = __double_as_longlong(x), by = __double_as_longlong(y), bz = __double_as_longlong(z);
+  long long mn = bx < by ? bx : by;
+  mn = mn < bz ? mn : bz;
+  const int same = (__double2hiint(a) ^ __double2hiint(b)) >= 0;
+  return __longlong_as_double(same ? mn : 0ll);
+}
 __device__ __forceinline__ double limited_slope(double a, double b, double hb) {
-  const double x = hb * a, z = hb * b, y = 0.25 * (a + b);
-  const unsigned long long mask = 0x7fffffffffffffffull;
-  const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & mask;
-  const unsigned long long ay = (unsigned long long)__double_as_longlong(y) & mask;
-  const unsigned long long az = (unsigned long long)__double_as_longlong(z) & mask;
-  unsigned long long mn = ax < ay ? ax : ay;
-  mn = mn < az ? mn : az;
-  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
-  const unsigned long long sgn = (unsigned long long)ba & ~mask;
-  return __longlong_as_double((long long)(((ba ^ bb) >= 0) ? (mn | sgn) : 0ull));
+  return minmod_sel(a, b, hb * a, 0.25 * (a + b), hb * b);
 }
 __device__ __forceinline__ float limited_slope(float a, float b, float hb) {
   const float x = hb * a, z = hb * b, y = 0.25f * (a + b);
@@ -330,16 +333,93 @@ __device__ __forceinline__ float limited_slope(float a, float b, float hb) {
 // along a stride; SGN = sign of the velocity component (never 0 here).
 //   v > 0: faces f_{j-1} + sigma_{j-1}, f_j + sigma_j
 //   v < 0: faces f_j - sigma_j, f_{j+1} - sigma_{j+1}
+// The candidate hb * D of the difference shared by the two slopes is formed once.
+__device__ __forceinline__ double flux_difference_d(const double* __restrict__ ptr, long long stride, double hb,
+                                                    int sgn) {
+  if (sgn > 0) {
+    const double fm2 = __ldg(ptr - 2 * stride), fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride);
+    const double Dm = fm1 - fm2, D0 = f0 - fm1, Dp = fp1 - f0;
+    const double rm = hb * Dm, r0 = hb * D0, rp = hb * Dp;
+    const double s0 = minmod_sel(D0, Dp, r0, 0.25 * (D0 + Dp), rp);
+    const double sm = minmod_sel(Dm, D0, rm, 0.25 * (Dm + D0), r0);
+    return D0 + s0 - sm;
+  } else {
+    const double fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride), fp2 = __ldg(ptr + 2 * stride);
+    const double D0 = f0 - fm1, Dp = fp1 - f0, Dpp = fp2 - fp1;
+    const double r0 = hb * D0, rp = hb * Dp, rpp = hb * Dpp;
+    const double sp = minmod_sel(Dp, Dpp, rp, 0.25 * (Dp + Dpp), rpp);
+    const double s0 = minmod_sel(D0, Dp, r0, 0.25 * (D0 + Dp), rp);
+    return Dp - sp + s0;
+  }
+}
+// ---- FP64 advection in block floating point on the integer pipe ----------
+// GB300 runs FP64 at 1/64 of the FP32 rate, while integer ops are cheap.  The
+// four values of one upwind stencil are brought to their largest exponent E
+// as 60-bit integers X = M 2^(e - E + 7) (M the 53-bit significand), so that
+// differences, the beta/2 scaling, the minmod selection and the flux
+// difference are exact integer arithmetic (truncation only below 2^-60 of the
+// largest value); only the result is converted back to double.  The
+// conversions are pure bit manipulation.
+__device__ __forceinline__ int bexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+__device__ __forceinline__ long long to_block_fixed(double v, int E) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int e = (hi >> 20) & 0x7ff;
+  const unsigned long long m = ((unsigned long long)((unsigned)(hi & 0xfffff) | 0x100000u) << 32) | lo;
+  const int sh = min(E - e, 63);
+  unsigned long long mag = (m << 7) >> sh;
+  mag = e == 0 ? 0ull : mag;  // zero (and subnormal) inputs
+  return hi < 0 ? -(long long)mag : (long long)mag;
+}
+
+// value of integer F at block exponent E: F 2^(E - 1075 - 7)
+__device__ __forceinline__ double from_block_fixed(long long F, int E) {
+  if (F == 0 || E < 64) return 0.0;
+  const double d = __ll2double_rn(F);
+  return __hiloint2double(__double2hiint(d) + ((E - 1082) << 20), __double2loint(d));
+}
+
+// limited slope on integers: minmod3(hb Da, (Da + Db)/4, hb Db); Hq = hb 2^62
+__device__ __forceinline__ long long slope_int(long long Da, long long Db, long long ra, long long rb) {
+  const long long y = (Da + Db) >> 2;
+  const long long mn = min(min(ra, y), rb), mx = max(max(ra, y), rb);
+  const bool same = (Da ^ Db) >= 0;
+  return same ? (Da >= 0 ? mn : mx) : 0ll;
+}
+
+__device__ __forceinline__ double flux_difference_int(const double* __restrict__ ptr, long long stride,
+                                                      long long Hq, int sgn) {
+  const long long o0 = sgn > 0 ? -2 * stride : -stride;
+  const double a0 = __ldg(ptr + o0), a1 = __ldg(ptr + o0 + stride), a2 = __ldg(ptr + o0 + 2 * stride),
+               a3 = __ldg(ptr + o0 + 3 * stride);
+  const int E = max(max(bexp(a0), bexp(a1)), max(bexp(a2), bexp(a3)));
+  const long long x0 = to_block_fixed(a0, E), x1 = to_block_fixed(a1, E), x2 = to_block_fixed(a2, E),
+                  x3 = to_block_fixed(a3, E);
+  const long long Da = x1 - x0, Db = x2 - x1, Dc = x3 - x2;
+  const long long ra = __mul64hi(Da << 2, Hq), rb = __mul64hi(Db << 2, Hq), rc = __mul64hi(Dc << 2, Hq);
+  const long long s_ab = slope_int(Da, Db, ra, rb);  // slope of the cell between a and b faces
+  const long long s_bc = slope_int(Db, Dc, rb, rc);
+  // v > 0 (cells j-2..j+1): dF = D_j + sigma_j - sigma_{j-1} = Db + s_bc - s_ab
+  // v < 0 (cells j-1..j+2): dF = D_{j+1} - sigma_{j+1} + sigma_j = Db - s_bc + s_ab
+  const long long F = sgn > 0 ? Db + s_bc - s_ab : Db - s_bc + s_ab;
+  return from_block_fixed(F, E);
+}
+
 template <int SGN, class T>
 __device__ __forceinline__ T flux_difference(const T* __restrict__ ptr, long long stride, T hb) {
-  if (SGN > 0) {
-    const T fm2 = __ldg(ptr - 2 * stride), fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride);
-    const T Dm = fm1 - fm2, D0 = f0 - fm1, Dp = fp1 - f0;
-    return D0 + limited_slope(D0, Dp, hb) - limited_slope(Dm, D0, hb);
+  if constexpr (sizeof(T) == 8) {
+    return flux_difference_d(ptr, stride, hb, SGN);
   } else {
-    const T fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride), fp2 = __ldg(ptr + 2 * stride);
-    const T D0 = f0 - fm1, Dp = fp1 - f0, Dpp = fp2 - fp1;
-    return Dp - limited_slope(Dp, Dpp, hb) + limited_slope(D0, Dp, hb);
+    if (SGN > 0) {
+      const T fm2 = __ldg(ptr - 2 * stride), fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride);
+      const T Dm = fm1 - fm2, D0 = f0 - fm1, Dp = fp1 - f0;
+      return D0 + limited_slope(D0, Dp, hb) - limited_slope(Dm, D0, hb);
+    } else {
+      const T fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride), fp2 = __ldg(ptr + 2 * stride);
+      const T D0 = f0 - fm1, Dp = fp1 - f0, Dpp = fp2 - fp1;
+      return Dp - limited_slope(Dp, Dpp, hb) + limited_slope(D0, Dp, hb);
+    }
   }
 }
 

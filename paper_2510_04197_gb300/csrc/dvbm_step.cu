@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
 
   typedef typename StoreT<S>::adv_t A;
   const A hb = (A)P.hb;
+  // FP32DEV: new deviation = a1 * dev + (t - k1 * ref) - advection, with the
+  // bracket (equilibrium evaluation minus the relaxed reference) in double
+  const double kref_f = -C.k1 * P.fref0, kref_g = -C.k1 * P.gref0;
+  const float a1f = (float)C.a1;
 
   // ---- phase B: populations, x-node by x-node ----
 #define DVBM_NODE(p)                                                                       \
@@ -83,22 +87,26 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
         const S* pc = s + c * PL;                                                           \
         const double t = k == 0 ? tf[q] : tg[q];                                            \
         A fx = 0, fy = 0;                                                                   \
-        if (sgn_of(p) > 0) fx = flux_difference<1, S>(pc, 1, (S)hb);                        \
-        if (sgn_of(p) < 0) fx = flux_difference<-1, S>(pc, 1, (S)hb);                       \
-        if (sgn_of(q) > 0) fy = flux_difference<1, S>(pc, PT, (S)hb);                       \
-        if (sgn_of(q) < 0) fy = flux_difference<-1, S>(pc, PT, (S)hb);                      \
+        if constexpr (sizeof(S) == 8) {                                                     \
+          if (sgn_of(p) != 0) fx = flux_difference_int((const double*)pc, 1, P.hq, sgn_of(p)); \
+          if (sgn_of(q) != 0) fy = flux_difference_int((const double*)pc, PT, P.hq, sgn_of(q)); \
+        } else {                                                                            \
+          if (sgn_of(p) > 0) fx = flux_difference<1, S>(pc, 1, (S)hb);                      \
+          if (sgn_of(p) < 0) fx = flux_difference<-1, S>(pc, 1, (S)hb);                     \
+          if (sgn_of(q) > 0) fy = flux_difference<1, S>(pc, PT, (S)hb);                     \
+          if (sgn_of(q) < 0) fy = flux_difference<-1, S>(pc, PT, (S)hb);                    \
+        }                                                                                   \
         if constexpr (sizeof(S) == 8) {                                                     \
           double v = fma(C.a1, (double)__ldg(pc), t);                                       \
           if (sgn_of(p) != 0) v = fma(-P.kxv[p], (double)fx, v);                            \
           if (sgn_of(q) != 0) v = fma(-P.kyv[q], (double)fy, v);                            \
           d[c * PL] = (S)v;                                                                 \
         } else {                                                                            \
-          const double ref = (k == 0 ? P.fref0 : P.gref0) * (w_of(p) * w_of(q));           \
-          const double base = fma(C.a1, (double)__ldg(pc), fma(-C.k1, ref, t));            \
+          const double base = fma(k == 0 ? kref_f : kref_g, w_of(p) * w_of(q), t);         \
           float adv = 0.f;                                                                  \
           if (sgn_of(p) != 0) adv = P.kxvf[p] * (float)fx;                                  \
           if (sgn_of(q) != 0) adv = fmaf(P.kyvf[q], (float)fy, adv);                        \
-          d[c * PL] = (S)(__double2float_rn(base) - adv);                                   \
+          d[c * PL] = (S)(fmaf(a1f, (float)__ldg(pc), __double2float_rn(base)) - adv);     \
         }                                                                                   \
       }                                                                                     \
     }                                                                                       \

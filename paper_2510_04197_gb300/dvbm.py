@@ -58,6 +58,7 @@ SIGNATURES = {
     "dvbm_steps_taken": (ctypes.c_longlong, [_VP]),
     "dvbm_last_error": (ctypes.c_char_p, [_VP]),
     "dvbm_destroy": (None, [_VP]),
+    "dvbm_cfl_dt_noalloc": (_CI, [_VP, _VP, _VP, _VP, ctypes.c_longlong, _CD, _CD, _CD, _CD, _VP, _DP]),
 }
 
 _lib = None

@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-fp32dev", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512, help="oracle sample grid size")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -57,12 +58,16 @@ def workload_config(N):
             "parallelism": "replicas (one independent grid per GPU)"}
 
 
+STEP_KERNEL_SOURCES = ("dvbm_device.cuh", "dvbm_step.cu")
+
+
 def kernel_source_hash():
+    """Hash of the sources the step kernel is compiled from (the committed
+    ncu figures are only used while this hash matches)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2510_04197_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, fn), "rb").read())
+    for fn in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -176,6 +181,48 @@ def run_reference(args, rank, world):
             "config": workload_config(args.size), "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def adjoint_ratio(dvbm, inputs, torch, N=512, nsteps=200):
+    """Adjoint workload: N^2 periodic FP64, multimode rms Ma 0.3 (seed 0),
+    Pr 0.71, gamma 1.4, mu 1e-3, nsteps steps, loss 1/(2N^2) sum[(rho - rho_t)^2
+    + (T - T_t)^2] against the same flow from seed 1 after nsteps steps;
+    checkpoints every ceil(sqrt(nsteps)).  Returns the time of the recorded
+    forward run and of dvbm_adjoint (segment recompute + adjoint steps)."""
+    import math as _m
+    every = int(_m.ceil(_m.sqrt(nsteps)))
+    tgt = inputs.multimode(N, seed=1, rms_Ma=0.3)
+    st = dvbm.Simulation(N, N, 0.71, 1.4, 1e-3, check_every=-1)
+    st.init(*(torch.tensor(a) for a in (tgt.rho, tgt.ux, tgt.uy, tgt.T)))
+    st.step(nsteps)
+    mt = st.moments()
+    dt = st.dt
+    st.close()
+    F = inputs.multimode(N, seed=0, rms_Ma=0.3)
+    fields = [torch.tensor(a, device="cuda") for a in (F.rho, F.ux, F.uy, F.T)]
+    out = {}
+    for rep in range(2):  # first repetition warms up allocations
+        sim = dvbm.Simulation(N, N, 0.71, 1.4, 1e-3, check_every=-1, dt=dt)
+        sim.record(every)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init(*fields)
+        sim.step(nsteps)
+        m = sim.moments()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        n2 = N * N
+        g = sim.adjoint((m["rho"] - mt["rho"]) / n2, (m["T"] - mt["T"]) / n2)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        sim.close()
+        out = {"workload": f"adjoint {N}x{N} periodic multimode rms Ma 0.3, {nsteps} FP64 steps, "
+                           f"checkpoints every {every}",
+               "t_forward_ms": (t1 - t0) * 1e3, "t_adjoint_ms": (t2 - t1) * 1e3,
+               "ratio": (t2 - t1) / (t1 - t0),
+               "grad_norms": {k: float(g[k].norm()) for k in ("rho0", "ux0", "uy0", "T0")},
+               "dL_dparams": [g["mu"], g["Pr"], g["gamma"]]}
+    return out
 
 
 def timed_steps(sim, K, stream):
@@ -311,6 +358,8 @@ def main():
                            "roofline_hbm": {"bound": "hbm", "achieved": g32, "peak": hbm_peak, "unit": "GB/s",
                                             "frac": g32 / hbm_peak}}
     line["e2e"] = e2e
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_ratio(dvbm, inputs, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     print(json.dumps(line), flush=True)

@@ -137,6 +137,25 @@ size_t dvbm_state_bytes(const dvbm_ctx* ctx);
 dvbm_status dvbm_get_state(dvbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 dvbm_status dvbm_set_state(dvbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
 
+/* Record the forward run for dvbm_adjoint: from the next dvbm_init on, keep
+ * the initial fields and a device copy of the state every `every` steps
+ * (checkpoints; sqrt(n) is the usual choice).  every = 0 turns recording off.
+ * Needs FP64 storage and periodic boundaries.  dvbm_set_state discards the
+ * recording.  Errors: EINVAL. */
+dvbm_status dvbm_record(dvbm_ctx* ctx, int every);
+
+/* Discrete adjoint of the recorded run (a training pattern the paper does not
+ * have; the forward map is Eq. finalDiscretePDE with equilibrium initial
+ * conditions, dt held fixed).  Given device arrays [Ny][Nx] dL/drho and dL/dT
+ * of the current state (either may be NULL = 0), writes the device arrays
+ * dL/drho0, dL/dux0, dL/duy0, dL/dT0 of the initial fields and, to the host
+ * array g_params, dL/dmu, dL/dPr, dL/dgamma.  Each checkpoint segment is
+ * recomputed once, then stepped backwards with the hand-written adjoint step
+ * kernel.  The state of the context is left unchanged.  Synchronous.
+ * Errors: ESTATE (no recording), EINVAL, ENOMEM, ECUDA. */
+dvbm_status dvbm_adjoint(dvbm_ctx* ctx, const double* dL_drho, const double* dL_dT, double* g_rho0,
+                         double* g_ux0, double* g_uy0, double* g_T0, double g_params[3]);
+
 /* Time step size fixed at dvbm_init (0 before). */
 double dvbm_dt(const dvbm_ctx* ctx);
 

@@ -188,7 +188,7 @@ def relaxation_times(P: Params, rho, T):
     Pr <= 1: nu = mu/rho = tau_1 R T and Pr = tau_1/tau_2;
     Pr >= 1: nu = mu/rho = tau_2 R T and Pr = tau_2/tau_1."""
     p = rho * P.R * T
-    if float(P.Pr) <= 1.0:
+    if float(P.Pr.detach() if torch.is_tensor(P.Pr) else P.Pr) <= 1.0:
         tau1 = P.mu / p
         tau2 = tau1 / P.Pr
     else:
@@ -546,8 +546,16 @@ def step(lat: Lattice, P: Params, grid: Grid, f, g, dt):
     for F in {f_i, g_i}, everything evaluated at time t."""
     _check_bcs(grid)
     xlo, xhi, ylo, yhi = grid.bcs
-    fpx, gpx = pad_axis(lat, P, f, g, 2, xlo, xhi)
     fpy, gpy = pad_axis(lat, P, f, g, 1, ylo, yhi)
+    return step_with_y_halos(lat, P, grid, f, g, fpy, gpy, dt)
+
+
+def step_with_y_halos(lat: Lattice, P: Params, grid: Grid, f, g, fpy, gpy, dt):
+    """The same step with the y-padded arrays [Q, Ny + 4, Nx] supplied by the
+    caller (two halo rows on each side), e.g. rows received from neighbouring
+    slabs of a domain decomposed along y.  x uses grid.bcs."""
+    xlo, xhi, ylo, yhi = grid.bcs
+    fpx, gpx = pad_axis(lat, P, f, g, 2, xlo, xhi)
     rho, ux, uy, T, _ = macroscopic(lat, P, f, g)
     tau1, tau2 = relaxation_times(P, rho, T)
     feq, geq = equilibria(lat, P, rho, ux, uy, T)

@@ -1,0 +1,578 @@
+// dvbm_adjoint.cu -- hand-written discrete adjoint of the FP64 time step.
+//
+// For the map X^{n+1} = Phi(X^n; mu, Pr, gamma) of Eq. finalDiscretePDE (FP64
+// storage, periodic domain) the kernels compute lambda^n = (dPhi/dX^n)^T
+// lambda^{n+1} and the per-cell contributions to dL/d(mu, Pr, gamma):
+//
+//  * local (collision) part: with a1 = 1 - dt/tau1 and the combined Grad
+//    coefficients C (dvbm_device.cuh), X^{n+1}_k = a1 X_k + W_k sum C H_k - adv_k,
+//      lambda^n_i = a1 lambda_i + sum_j mbar_j dm_j/dX_i,
+//    where (abar1, Cbar) = (sum_k lambda_k X_k, sum_k lambda_k W_k H_k) are
+//    pulled back through the coefficient function by the reverse pass
+//    collision_coeffs_rev (the forward statements in reverse order), giving
+//    the moment adjoints mbar and the parameter adjoints;
+//  * advection part, written as a gather: the flux difference of cell c',
+//    F(c') = D_c' + sigma_c' - sigma_{c'-1} (v > 0) or
+//    D_{c'+1} - sigma_{c'+1} + sigma_c' (v < 0), with D_k = X_k - X_{k-1} and
+//    sigma_k = minmod3(hb D_k, (D_k + D_{k+1})/4, hb D_{k+1}); its adjoint
+//    needs X and lambda at c-2 .. c+2 only.  The minmod branch of each slope
+//    gives the partial derivatives (hb, 0), (1/4, 1/4), (0, hb) or (0, 0).
+//    As in the forward kernel the linear combinations run in block floating
+//    point on the integer pipe.
+#include "dvbm_device.cuh"
+#include "dvbm_cellmom.cuh"
+#include "dvbm_internal.h"
+
+namespace dvbm {
+
+// ---------------------------------------------------------------- reverse pass
+struct ParamBar { double dt_mu, Pr, gm1, epsf; };
+
+// Reverse of collision_coeffs<PRC> for the outputs C (f, g) and a1.
+template <int PRC>
+__device__ __forceinline__ void collision_coeffs_rev(const Moments& m, const Phys& P, const Coeffs& Cb,
+                                                     double a1b, Moments& mb, ParamBar& pb) {
+  // ---- forward recomputation of the intermediates
+  const double rho = m.m00;
+  const double irho = 1.0 / rho;
+  const double ux = m.m10 * irho, uy = m.m01 * irho;
+  const double Et = fma(0.5, m.m20 + m.m02, m.g00 * P.inv_c2);
+  const double q = fma(ux, ux, uy * uy);
+  const double w = fma(-0.5, q, Et * irho);
+  const double theta = P.gm1 * w;
+  const double s = theta - 1.0;
+  const double p = rho * P.c2 * theta;
+  double k1, k2;
+  if (PRC <= 0) { k1 = P.dt_mu * p; k2 = k1 * P.Pr; }
+  else          { k2 = P.dt_mu * p; k1 = k2 * P.Pr; }
+  const double s1 = k1 - k2;
+  const EqF e = eq_f(rho, ux, uy, s);
+  const double reps = rho * P.epsf * theta;
+  double Dxx = 0, Dxy = 0, Dyy = 0, kap = 0, Px = 0, Py = 0, Tx = 0;
+  double d20 = 0, d11 = 0, d02 = 0, d30 = 0, d21 = 0, d12 = 0, d03 = 0, d40 = 0, d31 = 0, d13 = 0, d04 = 0;
+  double dg10 = 0, dg01 = 0;
+  if (PRC != 0) {
+    Dxx = (m.m20 - rho) - e.a20;
+    Dxy = m.m11 - e.a11;
+    Dyy = (m.m02 - rho) - e.a02;
+    if (PRC < 0) {
+      kap = 0.25 * (Dxx + Dyy);
+      Px = Dxx - kap; Py = Dyy - kap;
+      d30 = (fma(-3.0, m.m10, m.m30) - e.a30) - 3.0 * ux * Px;
+      d21 = ((m.m21 - m.m01) - e.a21) - fma(2.0 * ux, Dxy, uy * Px);
+      d12 = ((m.m12 - m.m10) - e.a12) - fma(2.0 * uy, Dxy, ux * Py);
+      d03 = (fma(-3.0, m.m01, m.m03) - e.a03) - 3.0 * uy * Py;
+      dg10 = m.g10 * P.inv_c2 - reps * ux;
+      dg01 = m.g01 * P.inv_c2 - reps * uy;
+    } else {
+      Tx = 0.5 * (Dxx - Dyy);
+      d20 = Tx; d11 = Dxy; d02 = -Tx;
+      d30 = 3.0 * ux * Tx;
+      d21 = fma(uy, Tx, 2.0 * ux * Dxy);
+      d12 = fma(-ux, Tx, 2.0 * uy * Dxy);
+      d03 = -3.0 * uy * Tx;
+      d40 = -6.0 * Tx; d31 = -3.0 * Dxy; d13 = -3.0 * Dxy; d04 = 6.0 * Tx;
+    }
+  }
+  const double kg = k1 * P.c2, sg = s1 * P.c2;
+  const double KR = kg * reps;
+
+  // ---- reverse
+  double uxb = 0, uyb = 0, sb = 0, rhob = 0, thetab = 0, k1b = 0, k2b = 0, s1b = 0, repsb = 0;
+  // g outputs
+  double KRb = Cb.g00 + Cb.g10 * ux + Cb.g01 * uy + Cb.g20 * fma(ux, ux, s) + Cb.g11 * ux * uy + Cb.g02 * fma(uy, uy, s);
+  double sgb = Cb.g10 * dg10 + Cb.g01 * dg01;
+  const double dg10b = Cb.g10 * sg, dg01b = Cb.g01 * sg;
+  uxb += KR * (Cb.g10 + 2.0 * ux * Cb.g20 + uy * Cb.g11);
+  uyb += KR * (Cb.g01 + 2.0 * uy * Cb.g02 + ux * Cb.g11);
+  sb += KR * (Cb.g20 + Cb.g02);
+  const double kgb = KRb * reps;
+  repsb += KRb * kg;
+  k1b += kgb * P.c2;
+  s1b += sgb * P.c2;
+  // f outputs: C.fab = k1 a_ab + s1 d_ab
+  double a00b = Cb.f00 * k1, a10b = Cb.f10 * k1, a01b = Cb.f01 * k1, a20b = Cb.f20 * k1, a11b = Cb.f11 * k1,
+         a02b = Cb.f02 * k1, a30b = Cb.f30 * k1, a21b = Cb.f21 * k1, a12b = Cb.f12 * k1, a03b = Cb.f03 * k1,
+         a40b = Cb.f40 * k1, a31b = Cb.f31 * k1, a22b = Cb.f22 * k1, a13b = Cb.f13 * k1, a04b = Cb.f04 * k1;
+  k1b += Cb.f00 * e.a00 + Cb.f10 * e.a10 + Cb.f01 * e.a01 + Cb.f20 * e.a20 + Cb.f11 * e.a11 + Cb.f02 * e.a02 +
+         Cb.f30 * e.a30 + Cb.f21 * e.a21 + Cb.f12 * e.a12 + Cb.f03 * e.a03 + Cb.f40 * e.a40 + Cb.f31 * e.a31 +
+         Cb.f22 * e.a22 + Cb.f13 * e.a13 + Cb.f04 * e.a04;
+  s1b += Cb.f20 * d20 + Cb.f11 * d11 + Cb.f02 * d02 + Cb.f30 * d30 + Cb.f21 * d21 + Cb.f12 * d12 + Cb.f03 * d03 +
+         Cb.f40 * d40 + Cb.f31 * d31 + Cb.f13 * d13 + Cb.f04 * d04;
+  const double d20b = Cb.f20 * s1, d11b = Cb.f11 * s1, d02b = Cb.f02 * s1, d30b = Cb.f30 * s1, d21b = Cb.f21 * s1,
+               d12b = Cb.f12 * s1, d03b = Cb.f03 * s1, d40b = Cb.f40 * s1, d31b = Cb.f31 * s1, d13b = Cb.f13 * s1,
+               d04b = Cb.f04 * s1;
+  if (PRC != 0) {
+    double Dxxb = 0, Dxyb = 0, Dyyb = 0;
+    if (PRC < 0) {
+      // dg10 = g10 inv_c2 - reps ux ; dg01 = g01 inv_c2 - reps uy
+      mb.g10 += dg10b * P.inv_c2;
+      mb.g01 += dg01b * P.inv_c2;
+      repsb -= dg10b * ux + dg01b * uy;
+      uxb -= dg10b * reps;
+      uyb -= dg01b * reps;
+      double Pxb = 0, Pyb = 0;
+      // d03 = m03 - 3 m01 - a03 - 3 uy Py
+      mb.m03 += d03b; mb.m01 -= 3.0 * d03b; a03b -= d03b; uyb -= 3.0 * d03b * Py; Pyb -= 3.0 * d03b * uy;
+      // d12 = m12 - m10 - a12 - 2 uy Dxy - ux Py
+      mb.m12 += d12b; mb.m10 -= d12b; a12b -= d12b; uyb -= 2.0 * d12b * Dxy; Dxyb -= 2.0 * d12b * uy;
+      uxb -= d12b * Py; Pyb -= d12b * ux;
+      // d21 = m21 - m01 - a21 - 2 ux Dxy - uy Px
+      mb.m21 += d21b; mb.m01 -= d21b; a21b -= d21b; uxb -= 2.0 * d21b * Dxy; Dxyb -= 2.0 * d21b * ux;
+      uyb -= d21b * Px; Pxb -= d21b * uy;
+      // d30 = m30 - 3 m10 - a30 - 3 ux Px
+      mb.m30 += d30b; mb.m10 -= 3.0 * d30b; a30b -= d30b; uxb -= 3.0 * d30b * Px; Pxb -= 3.0 * d30b * ux;
+      // Px = Dxx - kap, Py = Dyy - kap, kap = (Dxx + Dyy)/4
+      const double kapb = -(Pxb + Pyb);
+      Dxxb += Pxb + 0.25 * kapb;
+      Dyyb += Pyb + 0.25 * kapb;
+    } else {
+      const double Txb = d20b - d02b + 3.0 * ux * d30b + uy * d21b - ux * d12b - 3.0 * uy * d03b - 6.0 * d40b + 6.0 * d04b;
+      Dxyb += d11b + 2.0 * ux * d21b + 2.0 * uy * d12b - 3.0 * d31b - 3.0 * d13b;
+      uxb += 3.0 * Tx * d30b + 2.0 * Dxy * d21b - Tx * d12b;
+      uyb += Tx * d21b + 2.0 * Dxy * d12b - 3.0 * Tx * d03b;
+      Dxxb += 0.5 * Txb;
+      Dyyb -= 0.5 * Txb;
+    }
+    // Dxx = m20 - rho - a20 ; Dxy = m11 - a11 ; Dyy = m02 - rho - a02
+    mb.m20 += Dxxb; rhob -= Dxxb; a20b -= Dxxb;
+    mb.m11 += Dxyb; a11b -= Dxyb;
+    mb.m02 += Dyyb; rhob -= Dyyb; a02b -= Dyyb;
+  }
+  // reps = rho epsf theta
+  rhob += repsb * P.epsf * theta;
+  pb.epsf += repsb * rho * theta;
+  thetab += repsb * rho * P.epsf;
+  // eq_f reverse (statements in reverse order)
+  double rsb = 0;
+  a20b += a22b * fma(uy, uy, s); uyb += a22b * e.a20 * 2.0 * uy; sb += a22b * e.a20;
+  a03b += a13b * ux; uxb += a13b * e.a03;
+  a30b += a31b * uy; uyb += a31b * e.a30;
+  a03b += a04b * uy; uyb += a04b * e.a03; sb += 3.0 * a04b * e.a02; a02b += 3.0 * s * a04b;
+  a30b += a40b * ux; uxb += a40b * e.a30; sb += 3.0 * a40b * e.a20; a20b += 3.0 * s * a40b;
+  a02b += a12b * ux; uxb += a12b * e.a02;
+  a20b += a21b * uy; uyb += a21b * e.a20;
+  a02b += a03b * uy; uyb += a03b * e.a02; sb += 2.0 * a03b * e.a01; a01b += 2.0 * s * a03b;
+  a20b += a30b * ux; uxb += a30b * e.a20; sb += 2.0 * a30b * e.a10; a10b += 2.0 * s * a30b;
+  a01b += a02b * uy; uyb += a02b * e.a01; rsb += a02b;
+  a10b += a11b * uy; uyb += a11b * e.a10;
+  a10b += a20b * ux; uxb += a20b * e.a10; rsb += a20b;
+  rhob += a01b * uy; uyb += a01b * rho;
+  rhob += a10b * ux; uxb += a10b * rho;
+  rhob += a00b;
+  rhob += rsb * s; sb += rsb * rho;
+  // a1 = 1 - k1 ; s1 = k1 - k2
+  k1b += s1b - a1b;
+  k2b -= s1b;
+  double pbar;
+  if (PRC <= 0) {  // k1 = dt_mu p ; k2 = k1 Pr
+    k1b += k2b * P.Pr; pb.Pr += k2b * k1;
+    pb.dt_mu += k1b * p; pbar = k1b * P.dt_mu;
+  } else {         // k2 = dt_mu p ; k1 = k2 Pr
+    k2b += k1b * P.Pr; pb.Pr += k1b * k2;
+    pb.dt_mu += k2b * p; pbar = k2b * P.dt_mu;
+  }
+  // p = rho c2 theta
+  rhob += pbar * P.c2 * theta;
+  thetab += pbar * rho * P.c2;
+  // s = theta - 1
+  thetab += sb;
+  // theta = gm1 w, w = Et irho - q/2
+  pb.gm1 += thetab * w;
+  const double wb = thetab * P.gm1;
+  const double Etb = wb * irho;
+  double irhob = wb * Et;
+  const double qb = -0.5 * wb;
+  uxb += 2.0 * ux * qb;
+  uyb += 2.0 * uy * qb;
+  mb.m20 += 0.5 * Etb; mb.m02 += 0.5 * Etb; mb.g00 += Etb * P.inv_c2;
+  mb.m10 += uxb * irho; irhob += uxb * m.m10;
+  mb.m01 += uyb * irho; irhob += uyb * m.m01;
+  rhob -= irhob * irho * irho;
+  mb.m00 += rhob;
+}
+
+// Reverse of the (rho, T) read-out of the moments (macro_from_moments): given
+// dL/drho and dL/dT, accumulate the moment adjoints and dL/d(gamma - 1).
+__device__ __forceinline__ void macro_rev(const Moments& m, const Phys& P, double T_ref, double rhob_in, double Tb,
+                                          Moments& mb, ParamBar& pb) {
+  const double rho = m.m00;
+  const double irho = 1.0 / rho;
+  const double ux = m.m10 * irho, uy = m.m01 * irho;
+  const double Et = fma(0.5, m.m20 + m.m02, m.g00 * P.inv_c2);
+  const double w = fma(-0.5, fma(ux, ux, uy * uy), Et * irho);
+  const double thetab = Tb * T_ref;
+  pb.gm1 += thetab * w;
+  const double wb = thetab * P.gm1;
+  const double Etb = wb * irho;
+  double irhob = wb * Et;
+  const double qb = -0.5 * wb;
+  const double uxb = 2.0 * ux * qb, uyb = 2.0 * uy * qb;
+  mb.m20 += 0.5 * Etb; mb.m02 += 0.5 * Etb; mb.g00 += Etb * P.inv_c2;
+  mb.m10 += uxb * irho; irhob += uxb * m.m10;
+  mb.m01 += uyb * irho; irhob += uyb * m.m01;
+  mb.m00 += rhob_in - irhob * irho * irho;
+}
+
+// Reverse of equilibrium_coeffs (initial conditions): from Cbar to the
+// adjoints of rho, u (units of c), theta and epsf.
+__device__ __forceinline__ void equilibrium_rev(double rho, double ux, double uy, double theta, const Phys& P,
+                                                const Coeffs& Cb, double& rhob, double& uxb, double& uyb,
+                                                double& thetab, double& epsfb) {
+  const double s = theta - 1.0;
+  const EqF e = eq_f(rho, ux, uy, s);
+  const double reps = rho * P.epsf * theta * P.c2;
+  double sb = 0;
+  const double repsb = Cb.g00 + Cb.g10 * ux + Cb.g01 * uy + Cb.g20 * fma(ux, ux, s) + Cb.g11 * ux * uy +
+                       Cb.g02 * fma(uy, uy, s);
+  uxb = reps * (Cb.g10 + 2.0 * ux * Cb.g20 + uy * Cb.g11);
+  uyb = reps * (Cb.g01 + 2.0 * uy * Cb.g02 + ux * Cb.g11);
+  sb += reps * (Cb.g20 + Cb.g02);
+  rhob = repsb * P.epsf * theta * P.c2;
+  epsfb = repsb * rho * theta * P.c2;
+  thetab = repsb * rho * P.epsf * P.c2;
+  double a00b = Cb.f00, a10b = Cb.f10, a01b = Cb.f01, a20b = Cb.f20, a11b = Cb.f11, a02b = Cb.f02, a30b = Cb.f30,
+         a21b = Cb.f21, a12b = Cb.f12, a03b = Cb.f03, a40b = Cb.f40, a31b = Cb.f31, a22b = Cb.f22, a13b = Cb.f13,
+         a04b = Cb.f04;
+  double rsb = 0;
+  a20b += a22b * fma(uy, uy, s); uyb += a22b * e.a20 * 2.0 * uy; sb += a22b * e.a20;
+  a03b += a13b * ux; uxb += a13b * e.a03;
+  a30b += a31b * uy; uyb += a31b * e.a30;
+  a03b += a04b * uy; uyb += a04b * e.a03; sb += 3.0 * a04b * e.a02; a02b += 3.0 * s * a04b;
+  a30b += a40b * ux; uxb += a40b * e.a30; sb += 3.0 * a40b * e.a20; a20b += 3.0 * s * a40b;
+  a02b += a12b * ux; uxb += a12b * e.a02;
+  a20b += a21b * uy; uyb += a21b * e.a20;
+  a02b += a03b * uy; uyb += a03b * e.a02; sb += 2.0 * a03b * e.a01; a01b += 2.0 * s * a03b;
+  a20b += a30b * ux; uxb += a30b * e.a20; sb += 2.0 * a30b * e.a10; a10b += 2.0 * s * a30b;
+  a01b += a02b * uy; uyb += a02b * e.a01; rsb += a02b;
+  a10b += a11b * uy; uyb += a11b * e.a10;
+  a10b += a20b * ux; uxb += a20b * e.a10; rsb += a20b;
+  rhob += a01b * uy; uyb += a01b * rho;
+  rhob += a10b * ux; uxb += a10b * rho;
+  rhob += a00b;
+  rhob += rsb * s; sb += rsb * rho;
+  thetab += sb;
+}
+
+// ------------------------------------------------------- projections / moments
+// Cbar_ab = sum over the node's populations of lambda W W He_a He_b /(a! b!):
+// accumulate the contribution of x-node p (lf, lg: the 5 f and g values).
+template <int p>
+__device__ __forceinline__ void accumulate_projection(Coeffs& Cb, const double (&lf)[5], const double (&lg)[5]) {
+  double hb[5];  // hbar^b_p = sum_q lambda_pq kh(q, b)
+  {
+    const double sA = lf[1] + lf[2], dA = lf[1] - lf[2], sB = lf[3] + lf[4], dB = lf[3] - lf[4];
+    hb[0] = fma(kh(3, 0), sB, fma(kh(1, 0), sA, kh(0, 0) * lf[0]));
+    hb[1] = fma(kh(3, 1), dB, kh(1, 1) * dA);
+    hb[2] = fma(kh(3, 2), sB, fma(kh(1, 2), sA, kh(0, 2) * lf[0]));
+    hb[3] = fma(kh(3, 3), dB, kh(1, 3) * dA);
+    hb[4] = fma(kh(3, 4), sB, fma(kh(1, 4), sA, kh(0, 4) * lf[0]));
+  }
+  Cb.f00 = fma(kh(p, 0), hb[0], Cb.f00);
+  Cb.f01 = fma(kh(p, 0), hb[1], Cb.f01);
+  Cb.f02 = fma(kh(p, 0), hb[2], Cb.f02);
+  Cb.f03 = fma(kh(p, 0), hb[3], Cb.f03);
+  Cb.f04 = fma(kh(p, 0), hb[4], Cb.f04);
+  Cb.f20 = fma(kh(p, 2), hb[0], Cb.f20);
+  Cb.f21 = fma(kh(p, 2), hb[1], Cb.f21);
+  Cb.f22 = fma(kh(p, 2), hb[2], Cb.f22);
+  Cb.f40 = fma(kh(p, 4), hb[0], Cb.f40);
+  if (p != 0) {
+    Cb.f10 = fma(kh(p, 1), hb[0], Cb.f10);
+    Cb.f11 = fma(kh(p, 1), hb[1], Cb.f11);
+    Cb.f12 = fma(kh(p, 1), hb[2], Cb.f12);
+    Cb.f13 = fma(kh(p, 1), hb[3], Cb.f13);
+    Cb.f30 = fma(kh(p, 3), hb[0], Cb.f30);
+    Cb.f31 = fma(kh(p, 3), hb[1], Cb.f31);
+  }
+  double gb[3];
+  {
+    const double sA = lg[1] + lg[2], dA = lg[1] - lg[2], sB = lg[3] + lg[4], dB = lg[3] - lg[4];
+    gb[0] = fma(kh(3, 0), sB, fma(kh(1, 0), sA, kh(0, 0) * lg[0]));
+    gb[1] = fma(kh(3, 1), dB, kh(1, 1) * dA);
+    gb[2] = fma(kh(3, 2), sB, fma(kh(1, 2), sA, kh(0, 2) * lg[0]));
+  }
+  Cb.g00 = fma(kh(p, 0), gb[0], Cb.g00);
+  Cb.g01 = fma(kh(p, 0), gb[1], Cb.g01);
+  Cb.g02 = fma(kh(p, 0), gb[2], Cb.g02);
+  Cb.g20 = fma(kh(p, 2), gb[0], Cb.g20);
+  if (p != 0) {
+    Cb.g10 = fma(kh(p, 1), gb[0], Cb.g10);
+    Cb.g11 = fma(kh(p, 1), gb[1], Cb.g11);
+  }
+}
+
+// sum_j mbar_j dm_j/dX for the populations (p, q) of one x-node:
+// f: sum_{a+b<=3} mbar_ab xi_p^a xi_q^b ; g: gbar00 + gbar10 xi_p + gbar01 xi_q
+template <int p>
+__device__ __forceinline__ void moment_pullback(const Moments& mb, double (&pf)[5], double (&pg)[5]) {
+  constexpr double x = xi_of(p);
+  const double b0 = fma(x * x * x, mb.m30, fma(x * x, mb.m20, fma(x, mb.m10, mb.m00)));
+  const double b1 = fma(x * x, mb.m21, fma(x, mb.m11, mb.m01));
+  const double b2 = fma(x, mb.m12, mb.m02);
+  const double b3 = mb.m03;
+  const double g0 = fma(x, mb.g10, mb.g00);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const double y = xi_of(q);
+    pf[q] = fma(y * y * y, b3, fma(y * y, b2, fma(y, b1, b0)));
+    pg[q] = fma(y, mb.g01, g0);
+  }
+}
+
+// ------------------------------------------------------------ advection adjoint
+// minmod branch of sigma(Da, Db) with block-fixed integers: 0 zero, 1 hb Da,
+// 2 (Da + Db)/4, 3 hb Db.  Ties resolve in the order hb Da, (Da+Db)/4, hb Db.
+__device__ __forceinline__ int slope_branch(long long Da, long long Db, long long ra, long long rb) {
+  if ((Da ^ Db) < 0) return 0;
+  const long long y = (Da + Db) >> 2;
+  if (Da >= 0) {
+    if (ra <= y && ra <= rb) return 1;
+    return y <= rb ? 2 : 3;
+  }
+  if (ra >= y && ra >= rb) return 1;
+  return y >= rb ? 2 : 3;
+}
+// partial derivatives (first, second argument) times an integer sbar
+__device__ __forceinline__ long long slope_d1(int br, long long sbar, long long Hq) {
+  return br == 1 ? __mul64hi(sbar << 2, Hq) : (br == 2 ? (sbar >> 2) : 0ll);
+}
+__device__ __forceinline__ long long slope_d2(int br, long long sbar, long long Hq) {
+  return br == 3 ? __mul64hi(sbar << 2, Hq) : (br == 2 ? (sbar >> 2) : 0ll);
+}
+
+// lambda values at block exponent with 6 fraction-guard bits less than the
+// forward conversion (headroom for the sums below)
+__device__ __forceinline__ long long to_block_fixed6(double v, int E) { return to_block_fixed(v, E) >> 1; }
+
+// Adjoint of the flux difference of one population along one axis, gathered
+// at cell c: returns sum_{c'} lambda(c') dF(c')/dX(c) (multiply by -k outside).
+__device__ __forceinline__ double advection_adjoint(const double* __restrict__ X, const double* __restrict__ L,
+                                                    long long stride, long long Hq, int sgn) {
+  double xv[5], lv[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    xv[k] = __ldg(X + (k - 2) * stride);
+    lv[k] = __ldg(L + (k - 2) * stride);
+  }
+  const int EX = max(max(max(bexp(xv[0]), bexp(xv[1])), max(bexp(xv[2]), bexp(xv[3]))), bexp(xv[4]));
+  long long xi[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) xi[k] = to_block_fixed(xv[k], EX);
+  // differences D_{c-1} .. D_{c+2} (index 0..3) and slope branches of
+  // sigma_{c-1} (D_{c-1}, D_c), sigma_c (D_c, D_{c+1}), sigma_{c+1} (D_{c+1}, D_{c+2})
+  long long D[4], r[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    D[k] = xi[k + 1] - xi[k];
+    r[k] = __mul64hi(D[k] << 2, Hq);
+  }
+  const int bm = slope_branch(D[0], D[1], r[0], r[1]);
+  const int b0 = slope_branch(D[1], D[2], r[1], r[2]);
+  const int bp = slope_branch(D[2], D[3], r[2], r[3]);
+  const int EL = max(max(max(bexp(lv[0]), bexp(lv[1])), max(bexp(lv[2]), bexp(lv[3]))), bexp(lv[4]));
+  long long l[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) l[k] = to_block_fixed6(lv[k], EL);
+  long long Xb;
+  if (sgn > 0) {
+    // sbar_k = l_k - l_{k+1}; Dbar_c = l_c + d1(sigma_c) sbar_c + d2(sigma_{c-1}) sbar_{c-1}
+    const long long sbm = l[1] - l[2], sb0 = l[2] - l[3], sbp = l[3] - l[4];
+    const long long Dc = l[2] + slope_d1(b0, sb0, Hq) + slope_d2(bm, sbm, Hq);
+    const long long Dc1 = l[3] + slope_d1(bp, sbp, Hq) + slope_d2(b0, sb0, Hq);
+    Xb = Dc - Dc1;
+  } else {
+    // sbar_k = l_k - l_{k-1}; Dbar_k = l_{k-1} + d1(sigma_k) sbar_k + d2(sigma_{k-1}) sbar_{k-1}
+    const long long sbm = l[1] - l[0], sb0 = l[2] - l[1], sbp = l[3] - l[2];
+    const long long Dc = l[1] + slope_d1(b0, sb0, Hq) + slope_d2(bm, sbm, Hq);
+    const long long Dc1 = l[2] + slope_d1(bp, sbp, Hq) + slope_d2(b0, sb0, Hq);
+    Xb = Dc - Dc1;
+  }
+  // value at exponent EL with 6 fraction bits: Xb 2^(EL - 1075 - 6)
+  if (Xb == 0 || EL < 64) return 0.0;
+  const double d = __ll2double_rn(Xb);
+  return __hiloint2double(__double2hiint(d) + ((EL - 1081) << 20), __double2loint(d));
+}
+
+// ------------------------------------------------------------------- kernels
+// One adjoint step: Lout = (dPhi/dX)^T Lin at state X; per-block sums of the
+// parameter adjoints (dt_mu, Pr, gm1, epsf) into partial[blk*4 + k].
+template <int PRC>
+__global__ void __launch_bounds__(256) k_adjoint_step(const double* __restrict__ X, const double* __restrict__ Lin,
+                                                      double* __restrict__ Lout, double* __restrict__ partial,
+                                                      Geom G, Phys P) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const bool active = x < G.Nx && y < G.Ny;
+  ParamBar pb = {0, 0, 0, 0};
+  if (active) {
+    const long long off = cell_index(G, y, x);
+    const double* xs = X + off;
+    const double* ls = Lin + off;
+    double* lo = Lout + off;
+    const long long PL = G.plane, PT = G.pitch;
+    Moments m = {};
+    Coeffs Cb = {};
+    double a1b = 0.0;
+    {
+      double f[5], g[5], lf[5], lg[5];
+#define DVBM_ADJ_A(p)                                                                  \
+      _Pragma("unroll") for (int q = 0; q < 5; ++q) {                                  \
+        f[q] = __ldg(xs + (5 * p + q) * PL); g[q] = __ldg(xs + (25 + 5 * p + q) * PL);  \
+        lf[q] = __ldg(ls + (5 * p + q) * PL); lg[q] = __ldg(ls + (25 + 5 * p + q) * PL); \
+        a1b = fma(lf[q], f[q], fma(lg[q], g[q], a1b));                                \
+      }                                                                                \
+      accumulate_moments<p>(m, f, g);                                                  \
+      accumulate_projection<p>(Cb, lf, lg);
+      DVBM_ADJ_A(0) DVBM_ADJ_A(1) DVBM_ADJ_A(2) DVBM_ADJ_A(3) DVBM_ADJ_A(4)
+#undef DVBM_ADJ_A
+    }
+    const Coeffs C = collision_coeffs<PRC>(m, P);
+    Moments mb = {};
+    collision_coeffs_rev<PRC>(m, P, Cb, a1b, mb, pb);
+#define DVBM_ADJ_B(p)                                                                       \
+    {                                                                                       \
+      double pf[5], pg[5];                                                                  \
+      moment_pullback<p>(mb, pf, pg);                                                       \
+      _Pragma("unroll") for (int q = 0; q < 5; ++q) {                                       \
+        _Pragma("unroll") for (int k = 0; k < 2; ++k) {                                     \
+          const int c = 5 * p + q + 25 * k;                                                 \
+          const double* xc = xs + c * PL;                                                   \
+          const double* lc = ls + c * PL;                                                   \
+          double v = fma(C.a1, __ldg(lc), k == 0 ? pf[q] : pg[q]);                          \
+          if (sgn_of(p) != 0) v = fma(-P.kxv[p], advection_adjoint(xc, lc, 1, P.hq, sgn_of(p)), v);  \
+          if (sgn_of(q) != 0) v = fma(-P.kyv[q], advection_adjoint(xc, lc, PT, P.hq, sgn_of(q)), v); \
+          lo[c * PL] = v;                                                                   \
+        }                                                                                   \
+      }                                                                                     \
+    }
+    DVBM_ADJ_B(0) DVBM_ADJ_B(1) DVBM_ADJ_B(2) DVBM_ADJ_B(3) DVBM_ADJ_B(4)
+#undef DVBM_ADJ_B
+  }
+  // block reduction of the parameter adjoints (fixed order)
+  __shared__ double sh[4][256];
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  sh[0][t] = pb.dt_mu; sh[1][t] = pb.Pr; sh[2][t] = pb.gm1; sh[3][t] = pb.epsf;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sh[k][t] += sh[k][t + w];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) partial[4 * b + k] = sh[k][0];
+  }
+}
+
+// lambda^N from dL/drho and dL/dT of the final state; partial: gm1 adjoint
+__global__ void __launch_bounds__(256) k_adjoint_final(const double* __restrict__ X, const double* __restrict__ rhob,
+                                                       const double* __restrict__ Tb, double* __restrict__ Lout,
+                                                       double* __restrict__ partial, Geom G, Phys P, Macro M) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const bool active = x < G.Nx && y < G.Ny;
+  ParamBar pb = {0, 0, 0, 0};
+  if (active) {
+    const long long off = cell_index(G, y, x);
+    const long long i = (long long)y * G.Nx + x;
+    const Moments m = cell_moments<double>(X + off, G.plane, P);
+    Moments mb = {};
+    macro_rev(m, P, M.T_ref, rhob ? rhob[i] : 0.0, Tb ? Tb[i] : 0.0, mb, pb);
+#define DVBM_FIN(p)                                                          \
+    {                                                                        \
+      double pf[5], pg[5];                                                   \
+      moment_pullback<p>(mb, pf, pg);                                        \
+      _Pragma("unroll") for (int q = 0; q < 5; ++q) {                        \
+        Lout[off + (5 * p + q) * G.plane] = pf[q];                           \
+        Lout[off + (25 + 5 * p + q) * G.plane] = pg[q];                      \
+      }                                                                      \
+    }
+    DVBM_FIN(0) DVBM_FIN(1) DVBM_FIN(2) DVBM_FIN(3) DVBM_FIN(4)
+#undef DVBM_FIN
+  }
+  __shared__ double sh[256];
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  sh[t] = pb.gm1;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) sh[t] += sh[t + w];
+    __syncthreads();
+  }
+  if (t == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// adjoint of the equilibrium initial condition: per-cell dL/d(rho0, ux0, uy0, T0)
+// and per-block epsf adjoints
+__global__ void __launch_bounds__(256) k_adjoint_init(const double* __restrict__ L, const double* __restrict__ rho,
+                                                      const double* __restrict__ ux, const double* __restrict__ uy,
+                                                      const double* __restrict__ T, double* grho, double* gux,
+                                                      double* guy, double* gT, double* __restrict__ partial, Geom G,
+                                                      Phys P, Macro M) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const bool active = x < G.Nx && y < G.Ny;
+  double epsfb = 0.0;
+  if (active) {
+    const long long off = cell_index(G, y, x);
+    const long long i = (long long)y * G.Nx + x;
+    Coeffs Cb = {};
+    {
+      double lf[5], lg[5];
+#define DVBM_INI(p)                                                         \
+      _Pragma("unroll") for (int q = 0; q < 5; ++q) {                       \
+        lf[q] = L[off + (5 * p + q) * G.plane];                             \
+        lg[q] = L[off + (25 + 5 * p + q) * G.plane];                        \
+      }                                                                     \
+      accumulate_projection<p>(Cb, lf, lg);
+      DVBM_INI(0) DVBM_INI(1) DVBM_INI(2) DVBM_INI(3) DVBM_INI(4)
+#undef DVBM_INI
+    }
+    double rb, ub, vb, thb;
+    equilibrium_rev(rho[i], ux[i] / M.c, uy[i] / M.c, T[i] / M.T_ref, P, Cb, rb, ub, vb, thb, epsfb);
+    grho[i] = rb;
+    gux[i] = ub / M.c;
+    guy[i] = vb / M.c;
+    gT[i] = thb / M.T_ref;
+  }
+  __shared__ double sh[256];
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  sh[t] = epsfb;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) sh[t] += sh[t + w];
+    __syncthreads();
+  }
+  if (t == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// ------------------------------------------------------------------ wrappers
+int adjoint_blocks(const Geom& G) { return ((G.Nx + 31) / 32) * ((G.Ny + 7) / 8); }
+
+cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial, const Geom& G,
+                                const Phys& P, cudaStream_t st) {
+  dim3 block(32, 8), grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
+  if (P.prc < 0) k_adjoint_step<-1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  else if (P.prc > 0) k_adjoint_step<1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  else k_adjoint_step<0><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_final(const double* X, const double* rhob, const double* Tb, double* Lout, double* partial,
+                                 const Geom& G, const Phys& P, const Macro& M, cudaStream_t st) {
+  dim3 block(32, 8), grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
+  k_adjoint_final<<<grid, block, 0, st>>>(X, rhob, Tb, Lout, partial, G, P, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_init(const double* L, const double* rho, const double* ux, const double* uy,
+                                const double* T, double* grho, double* gux, double* guy, double* gT, double* partial,
+                                const Geom& G, const Phys& P, const Macro& M, cudaStream_t st) {
+  dim3 block(32, 8), grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
+  k_adjoint_init<<<grid, block, 0, st>>>(L, rho, ux, uy, T, grho, gux, guy, gT, partial, G, P, M);
+  return cudaGetLastError();
+}
+
+}  // namespace dvbm

@@ -1,4 +1,5 @@
 // dvbm_api.cu -- the C ABI declared in include/dvbm.h.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -35,6 +36,13 @@ struct dvbm_ctx {
   long long steps = 0;
   bool initialised = false;
   std::string err;
+  // adjoint recording: checkpoints of the state every record_every steps
+  int record_every = 0;
+  bool recorded = false;               // checkpoints cover steps 0 .. steps
+  std::vector<void*> ckpt;             // ckpt[j] = state at step j * record_every
+  std::vector<void*> pool;             // spare state buffers
+  double* init_fields = nullptr;       // rho, ux, uy, T of the recorded dvbm_init
+  size_t state_bytes_dev = 0;
 };
 
 static std::string g_create_error;
@@ -148,6 +156,7 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
     c->bc.Tw[s] = b[s].T_wall;
   }
   const size_t bytes = (size_t)NPOP * c->G.plane * c->elem;
+  c->state_bytes_dev = bytes;
   for (int k = 0; k < 2; ++k) {
     cudaError_t e = cudaMalloc(&c->buf[k], bytes);
     if (e != cudaSuccess) {
@@ -231,6 +240,42 @@ static dvbm_status stage_fields(dvbm_ctx* c, DevFields& F, const double* const i
   return DVBM_OK;
 }
 
+static dvbm_status take_buffer(dvbm_ctx* c, void** out) {
+  if (!c->pool.empty()) {
+    *out = c->pool.back();
+    c->pool.pop_back();
+    return DVBM_OK;
+  }
+  CUDA_TRY(c, cudaMalloc(out, c->state_bytes_dev));
+  return DVBM_OK;
+}
+
+static void clear_record(dvbm_ctx* c) {
+  for (void* p : c->ckpt) c->pool.push_back(p);
+  c->ckpt.clear();
+  c->recorded = false;
+}
+
+static dvbm_status push_checkpoint(dvbm_ctx* c) {
+  void* b = nullptr;
+  dvbm_status s = take_buffer(c, &b);
+  if (s != DVBM_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(b, c->buf[c->cur], c->state_bytes_dev, cudaMemcpyDeviceToDevice, c->stream));
+  c->ckpt.push_back(b);
+  return DVBM_OK;
+}
+
+extern "C" dvbm_status dvbm_record(dvbm_ctx* c, int every) {
+  if (!c) return DVBM_EINVAL;
+  if (every < 0) return fail(c, DVBM_EINVAL, "record interval must be >= 0");
+  if (every > 0 && c->storage != DVBM_FP64) return fail(c, DVBM_EINVAL, "the adjoint needs FP64 storage");
+  for (int s = 0; s < 4 && every > 0; ++s)
+    if (c->bcs[s].kind != DVBM_BC_PERIODIC) return fail(c, DVBM_EINVAL, "the adjoint is built for periodic domains");
+  clear_record(c);
+  c->record_every = every;
+  return DVBM_OK;
+}
+
 extern "C" dvbm_status dvbm_init(dvbm_ctx* c, const double* rho, const double* ux, const double* uy,
                                  const double* T, int on_device) {
   if (!c) return DVBM_EINVAL;
@@ -256,6 +301,17 @@ extern "C" dvbm_status dvbm_init(dvbm_ctx* c, const double* rho, const double* u
   s = fill_ghosts(c, c->buf[0]);
   if (s != DVBM_OK) return s;
   CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(unsigned int), c->stream));
+  clear_record(c);
+  if (c->record_every > 0) {
+    const size_t n = (size_t)c->Nx * c->Ny;
+    if (!c->init_fields) CUDA_TRY(c, cudaMalloc(&c->init_fields, 4 * n * sizeof(double)));
+    for (int k = 0; k < 4; ++k)
+      CUDA_TRY(c, cudaMemcpyAsync(c->init_fields + k * n, F.p[k], n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    s = push_checkpoint(c);
+    if (s != DVBM_OK) return s;
+    c->recorded = true;
+  }
   s = wait_stream(c);  // the staged host copies are freed on return
   if (s != DVBM_OK) return s;
   c->steps = 0;
@@ -276,6 +332,10 @@ extern "C" dvbm_status dvbm_step(dvbm_ctx* c, int n) {
     if (s != DVBM_OK) return s;
     c->cur = 1 - c->cur;
     ++c->steps;
+    if (c->recorded && c->steps % c->record_every == 0) {
+      s = push_checkpoint(c);
+      if (s != DVBM_OK) return s;
+    }
     if (every > 0 && (i + 1) % every == 0) {
       s = check_flag(c);
       if (s != DVBM_OK) return s;
@@ -370,6 +430,103 @@ extern "C" dvbm_status dvbm_set_state(dvbm_ctx* c, const void* buf, size_t bytes
   if (s != DVBM_OK) return s;
   c->steps = st;
   c->initialised = true;
+  clear_record(c);
+  return DVBM_OK;
+}
+
+// Backward pass over the recorded forward run: lambda^N from dL/d(rho, T) of
+// the current state, then segment by segment (last first) a recompute of the
+// segment's states from its checkpoint and the adjoint steps through it,
+// finally the adjoint of the equilibrium initial condition.
+extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const double* dL_dT, double* g_rho0,
+                                    double* g_ux0, double* g_uy0, double* g_T0, double g_params[3]) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->recorded || c->ckpt.empty() || !c->init_fields)
+    return fail(c, DVBM_ESTATE, "no recorded forward run: call dvbm_record(ctx, k) before dvbm_init, then dvbm_step");
+  if (!g_rho0 || !g_ux0 || !g_uy0 || !g_T0 || !g_params) return fail(c, DVBM_EINVAL, "null gradient pointer");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const long long n = c->steps;
+  const int k = c->record_every;
+  const int nblk = adjoint_blocks(c->G);
+  const size_t ncell = (size_t)c->Nx * c->Ny;
+  // work buffers: two adjoint states, k segment states, partial sums
+  void* lam[2] = {nullptr, nullptr};
+  std::vector<void*> seg;
+  double* part = nullptr;
+  const long long nslots = (n + 2) * (long long)nblk * 4;
+  dvbm_status s = DVBM_OK;
+  auto cleanup = [&]() {
+    for (int i = 0; i < 2; ++i) if (lam[i]) c->pool.push_back(lam[i]);
+    for (void* p : seg) c->pool.push_back(p);
+    if (part) cudaFree(part);
+  };
+  for (int i = 0; i < 2 && s == DVBM_OK; ++i) s = take_buffer(c, &lam[i]);
+  for (int i = 0; i < k && s == DVBM_OK; ++i) {
+    void* b = nullptr;
+    s = take_buffer(c, &b);
+    if (s == DVBM_OK) seg.push_back(b);
+  }
+  if (s == DVBM_OK && cudaMalloc(&part, nslots * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    s = fail(c, DVBM_ENOMEM, "cudaMalloc of adjoint partial sums failed");
+  }
+  if (s == DVBM_OK && cudaMemsetAsync(part, 0, nslots * sizeof(double), c->stream) != cudaSuccess)
+    s = fail(c, DVBM_ECUDA, "memset failed");
+  if (s != DVBM_OK) { cleanup(); return s; }
+  // periodic ghost copies for the adjoint buffers
+  BCDev per = c->bc;
+  for (int i = 0; i < 4; ++i) per.kind[i] = DVBM_BC_PERIODIC;
+  cudaError_t e = cudaSuccess;
+  int a = 0;
+  long long slot = 0;
+  e = launch_adjoint_final((const double*)c->buf[c->cur], dL_drho, dL_dT, (double*)lam[a], part + slot * nblk * 4,
+                           c->G, c->P, c->M, c->stream);
+  ++slot;
+  if (e == cudaSuccess) e = launch_ghost(0, lam[a], c->G, c->P, c->M, per, c->stream);
+  const long long nseg = (n + k - 1) / k;
+  for (long long j = nseg - 1; j >= 0 && e == cudaSuccess; --j) {
+    const long long S = j * k, E = std::min<long long>((j + 1) * k, n);
+    e = cudaMemcpyAsync(seg[0], c->ckpt[j], c->state_bytes_dev, cudaMemcpyDeviceToDevice, c->stream);
+    for (long long t = 0; t + 1 < E - S && e == cudaSuccess; ++t) {
+      e = launch_step(0, seg[t], seg[t + 1], c->G, c->P, c->flag, c->stream);
+      if (e == cudaSuccess) e = launch_ghost(0, seg[t + 1], c->G, c->P, c->M, c->bc, c->stream);
+    }
+    for (long long t = E - S - 1; t >= 0 && e == cudaSuccess; --t) {
+      e = launch_adjoint_step((const double*)seg[t], (const double*)lam[a], (double*)lam[1 - a],
+                              part + slot * nblk * 4, c->G, c->P, c->stream);
+      ++slot;
+      a = 1 - a;
+      if (e == cudaSuccess) e = launch_ghost(0, lam[a], c->G, c->P, c->M, per, c->stream);
+    }
+  }
+  const double* F0 = c->init_fields;
+  if (e == cudaSuccess)
+    e = launch_adjoint_init((const double*)lam[a], F0, F0 + ncell, F0 + 2 * ncell, F0 + 3 * ncell, g_rho0, g_ux0,
+                            g_uy0, g_T0, part + slot * nblk * 4, c->G, c->P, c->M, c->stream);
+  ++slot;
+  std::vector<double> h;
+  if (e == cudaSuccess) {
+    h.resize(slot * nblk * 4);
+    e = cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e != cudaSuccess) { cleanup(); return fail(c, DVBM_ECUDA, "adjoint: %s", cudaGetErrorString(e)); }
+  s = wait_stream(c);
+  cleanup();
+  if (s != DVBM_OK) return s;
+  // slot 0: final read-out (gm1 adjoint per block); slots 1..n: steps (dt_mu, Pr, gm1, epsf);
+  // last slot: initial condition (epsf adjoint per block)
+  double dtmu_b = 0, Pr_b = 0, gm1_b = 0, epsf_b = 0;
+  for (int b = 0; b < nblk; ++b) gm1_b += h[b];
+  for (long long t = 1; t < slot - 1; ++t)
+    for (int b = 0; b < nblk; ++b) {
+      const double* q = &h[(t * nblk + b) * 4];
+      dtmu_b += q[0]; Pr_b += q[1]; gm1_b += q[2]; epsf_b += q[3];
+    }
+  for (int b = 0; b < nblk; ++b) epsf_b += h[((slot - 1) * nblk) * 4 + b];
+  const double gm1 = c->gamma - 1.0;
+  g_params[0] = -dtmu_b * c->dt / (c->mu * c->mu);   // d(dt/mu)/dmu = -dt/mu^2
+  g_params[1] = Pr_b;
+  g_params[2] = gm1_b - epsf_b / (gm1 * gm1);        // epsf = 1/(gamma-1) - 1
   return DVBM_OK;
 }
 
@@ -383,5 +540,8 @@ extern "C" void dvbm_destroy(dvbm_ctx* c) {
   for (int k = 0; k < 2; ++k) if (c->buf[k]) cudaFree(c->buf[k]);
   if (c->flag) cudaFree(c->flag);
   if (c->partial) cudaFree(c->partial);
+  for (void* p : c->ckpt) cudaFree(p);
+  for (void* p : c->pool) cudaFree(p);
+  if (c->init_fields) cudaFree(c->init_fields);
   delete c;
 }

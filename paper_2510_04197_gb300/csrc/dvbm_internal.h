@@ -32,4 +32,14 @@ cudaError_t launch_speed(const double* rho, const double* ux, const double* uy, 
 cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G,
                         cudaStream_t st);
 
+// adjoint (FP64 storage, periodic)
+int adjoint_blocks(const Geom& G);
+cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial, const Geom& G,
+                                const Phys& P, cudaStream_t st);
+cudaError_t launch_adjoint_final(const double* X, const double* rhob, const double* Tb, double* Lout, double* partial,
+                                 const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
+cudaError_t launch_adjoint_init(const double* L, const double* rho, const double* ux, const double* uy,
+                                const double* T, double* grho, double* gux, double* guy, double* gT, double* partial,
+                                const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
+
 }  // namespace dvbm

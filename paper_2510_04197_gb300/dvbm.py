@@ -58,6 +58,8 @@ SIGNATURES = {
     "dvbm_steps_taken": (ctypes.c_longlong, [_VP]),
     "dvbm_last_error": (ctypes.c_char_p, [_VP]),
     "dvbm_destroy": (None, [_VP]),
+    "dvbm_record": (_CI, [_VP, _CI]),
+    "dvbm_adjoint": (_CI, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP]),
     "dvbm_cfl_dt_noalloc": (_CI, [_VP, _VP, _VP, _VP, ctypes.c_longlong, _CD, _CD, _CD, _CD, _VP, _DP]),
 }
 
@@ -223,6 +225,32 @@ class Simulation:
         buf = self.get_state() if buf is None else buf
         dt = torch.float64 if self.storage == FP64 else torch.float32
         return buf[:-8].view(dt).view(50, self.Ny, self.Nx)
+
+    def record(self, every: int):
+        """Keep checkpoints every `every` steps of the next init + step run."""
+        _check(lib().dvbm_record(self._h, int(every)), self._h)
+        return self
+
+    def adjoint(self, dL_drho=None, dL_dT=None):
+        """Gradients of a loss of the final (rho, T) fields with respect to the
+        initial fields and (mu, Pr, gamma), by the hand-written adjoint."""
+        torch = _torch()
+        args = []
+        keep = []
+        for a in (dL_drho, dL_dT):
+            if a is None:
+                args.append(None)
+            else:
+                t = self._field(a)
+                keep.append(t)
+                args.append(ctypes.c_void_p(t.data_ptr()))
+        out = {k: torch.empty((self.Ny, self.Nx), dtype=torch.float64, device=self.device)
+               for k in ("rho0", "ux0", "uy0", "T0")}
+        gp = (ctypes.c_double * 3)()
+        _check(lib().dvbm_adjoint(self._h, args[0], args[1], *[ctypes.c_void_p(out[k].data_ptr())
+                                                             for k in ("rho0", "ux0", "uy0", "T0")], gp), self._h)
+        out["mu"], out["Pr"], out["gamma"] = gp[0], gp[1], gp[2]
+        return out
 
     @property
     def dt(self) -> float:

@@ -30,8 +30,8 @@ struct ParamBar { double dt_mu, Pr, gm1, epsf; };
 
 // Reverse of collision_coeffs<PRC> for the outputs C (f, g) and a1.
 template <int PRC>
-__device__ __forceinline__ void collision_coeffs_rev(const Moments& m, const Phys& P, const Coeffs& Cb,
-                                                     double a1b, Moments& mb, ParamBar& pb) {
+__device__ __forceinline__ double collision_coeffs_rev(const Moments& m, const Phys& P, const Coeffs& Cb,
+                                                       double a1b, Moments& mb, ParamBar& pb) {
   // ---- forward recomputation of the intermediates
   const double rho = m.m00;
   const double irho = 1.0 / rho;
@@ -190,6 +190,7 @@ __device__ __forceinline__ void collision_coeffs_rev(const Moments& m, const Phy
   mb.m01 += uyb * irho; irhob += uyb * m.m01;
   rhob -= irhob * irho * irho;
   mb.m00 += rhob;
+  return 1.0 - k1;  // a1 of the forward step
 }
 
 // Reverse of the (rho, T) read-out of the moments (macro_from_moments): given
@@ -388,19 +389,74 @@ __device__ __forceinline__ double advection_adjoint(const double* __restrict__ X
     const long long Dc1 = l[2] + slope_d1(bp, sbp, Hq) + slope_d2(b0, sb0, Hq);
     Xb = Dc - Dc1;
   }
-  // value at exponent EL with 6 fraction bits: Xb 2^(EL - 1075 - 6)
-  if (Xb == 0 || EL < 64) return 0.0;
-  const double d = __ll2double_rn(Xb);
-  return __hiloint2double(__double2hiint(d) + ((EL - 1081) << 20), __double2loint(d));
+  // value at exponent EL: Xb 2^(EL - 1081)
+  if (EL < 64) return 0.0;
+  return ll_to_double_scaled(Xb, EL - 1081);
+}
+
+// Rational-beta variant (beta = lp/lq): every partial derivative times 4 lq is
+// a small integer (2 lp for beta/2, lq for 1/4), so the adjoint combinations
+// are exact integer arithmetic without high multiplies.  Returns 4 lq times
+// sum_{c'} lambda(c') dF(c')/dX(c).  lambda enters with a 50-bit significand.
+__device__ __forceinline__ int slope_branch_rat(long long Da, long long Db, long long lp2, long long lq) {
+  if ((Da ^ Db) < 0) return 0;
+  const long long ra = lp2 * Da, rb = lp2 * Db, y = lq * (Da + Db);
+  if (Da >= 0) {
+    if (ra <= y && ra <= rb) return 1;
+    return y <= rb ? 2 : 3;
+  }
+  if (ra >= y && ra >= rb) return 1;
+  return y >= rb ? 2 : 3;
+}
+
+__device__ __forceinline__ double advection_adjoint_rat(const double* __restrict__ X, const double* __restrict__ L,
+                                                        long long stride, int lp, int lq, int sgn) {
+  double xv[5], lv[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    xv[k] = __ldg(X + (k - 2) * stride);
+    lv[k] = __ldg(L + (k - 2) * stride);
+  }
+  const int EX = max(max(max(bexp(xv[0]), bexp(xv[1])), max(bexp(xv[2]), bexp(xv[3]))), bexp(xv[4]));
+  const long long lp2 = 2 * lp, q = lq, q4 = 4 * lq;
+  long long D[4];
+  {
+    long long xi[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) xi[k] = to_block_fixed52(xv[k], EX);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D[k] = xi[k + 1] - xi[k];
+  }
+  const int bm = slope_branch_rat(D[0], D[1], lp2, q);
+  const int b0 = slope_branch_rat(D[1], D[2], lp2, q);
+  const int bp = slope_branch_rat(D[2], D[3], lp2, q);
+  const int EL = max(max(max(bexp(lv[0]), bexp(lv[1])), max(bexp(lv[2]), bexp(lv[3]))), bexp(lv[4]));
+  long long l[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) l[k] = to_block_fixed(lv[k], EL) >> 10;
+  auto d1 = [&](int br, long long sb) { return br == 1 ? lp2 * sb : (br == 2 ? q * sb : 0ll); };
+  auto d2 = [&](int br, long long sb) { return br == 3 ? lp2 * sb : (br == 2 ? q * sb : 0ll); };
+  long long Xb;
+  if (sgn > 0) {
+    const long long sbm = l[1] - l[2], sb0 = l[2] - l[3], sbp = l[3] - l[4];
+    Xb = (q4 * l[2] + d1(b0, sb0) + d2(bm, sbm)) - (q4 * l[3] + d1(bp, sbp) + d2(b0, sb0));
+  } else {
+    const long long sbm = l[1] - l[0], sb0 = l[2] - l[1], sbp = l[3] - l[2];
+    Xb = (q4 * l[1] + d1(b0, sb0) + d2(bm, sbm)) - (q4 * l[2] + d1(bp, sbp) + d2(b0, sb0));
+  }
+  if (EL < 64) return 0.0;
+  return ll_to_double_scaled(Xb, EL - 1072);  // lambda was scaled by 2^(1072 - EL)
 }
 
 // ------------------------------------------------------------------- kernels
-// One adjoint step: Lout = (dPhi/dX)^T Lin at state X; per-block sums of the
-// parameter adjoints (dt_mu, Pr, gm1, epsf) into partial[blk*4 + k].
+// One adjoint step in two launches.
+// k_adjoint_local: Lout = a1 Lin + sum_j mbar_j dm_j/dX (collision part) at
+// state X; per-block sums of the parameter adjoints (dt_mu, Pr, gm1, epsf)
+// into partial[blk*4 + k].
 template <int PRC>
-__global__ void __launch_bounds__(256) k_adjoint_step(const double* __restrict__ X, const double* __restrict__ Lin,
-                                                      double* __restrict__ Lout, double* __restrict__ partial,
-                                                      Geom G, Phys P) {
+__global__ void __launch_bounds__(256) k_adjoint_local(const double* __restrict__ X, const double* __restrict__ Lin,
+                                                       double* __restrict__ Lout, double* __restrict__ partial,
+                                                       Geom G, Phys P) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   const bool active = x < G.Nx && y < G.Ny;
@@ -410,7 +466,7 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const double* __restrict__
     const double* xs = X + off;
     const double* ls = Lin + off;
     double* lo = Lout + off;
-    const long long PL = G.plane, PT = G.pitch;
+    const long long PL = G.plane;
     Moments m = {};
     Coeffs Cb = {};
     double a1b = 0.0;
@@ -427,23 +483,15 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const double* __restrict__
       DVBM_ADJ_A(0) DVBM_ADJ_A(1) DVBM_ADJ_A(2) DVBM_ADJ_A(3) DVBM_ADJ_A(4)
 #undef DVBM_ADJ_A
     }
-    const Coeffs C = collision_coeffs<PRC>(m, P);
     Moments mb = {};
-    collision_coeffs_rev<PRC>(m, P, Cb, a1b, mb, pb);
+    const double a1 = collision_coeffs_rev<PRC>(m, P, Cb, a1b, mb, pb);
 #define DVBM_ADJ_B(p)                                                                       \
     {                                                                                       \
       double pf[5], pg[5];                                                                  \
       moment_pullback<p>(mb, pf, pg);                                                       \
       _Pragma("unroll") for (int q = 0; q < 5; ++q) {                                       \
-        _Pragma("unroll") for (int k = 0; k < 2; ++k) {                                     \
-          const int c = 5 * p + q + 25 * k;                                                 \
-          const double* xc = xs + c * PL;                                                   \
-          const double* lc = ls + c * PL;                                                   \
-          double v = fma(C.a1, __ldg(lc), k == 0 ? pf[q] : pg[q]);                          \
-          if (sgn_of(p) != 0) v = fma(-P.kxv[p], advection_adjoint(xc, lc, 1, P.hq, sgn_of(p)), v);  \
-          if (sgn_of(q) != 0) v = fma(-P.kyv[q], advection_adjoint(xc, lc, PT, P.hq, sgn_of(q)), v); \
-          lo[c * PL] = v;                                                                   \
-        }                                                                                   \
+        lo[(5 * p + q) * PL] = fma(a1, __ldg(ls + (5 * p + q) * PL), pf[q]);                \
+        lo[(25 + 5 * p + q) * PL] = fma(a1, __ldg(ls + (25 + 5 * p + q) * PL), pg[q]);      \
       }                                                                                     \
     }
     DVBM_ADJ_B(0) DVBM_ADJ_B(1) DVBM_ADJ_B(2) DVBM_ADJ_B(3) DVBM_ADJ_B(4)
@@ -465,6 +513,32 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const double* __restrict__
 #pragma unroll
     for (int k = 0; k < 4; ++k) partial[4 * b + k] = sh[k][0];
   }
+}
+
+// k_adjoint_adv: Lout += -(dt/dx) v_x sum_c' Lin(c') dF_x(c')/dX(c) - (same in y),
+// one thread per (cell, population); blockIdx.z = population.
+template <bool RAT>
+__global__ void __launch_bounds__(256) k_adjoint_adv(const double* __restrict__ X, const double* __restrict__ Lin,
+                                                     double* __restrict__ Lout, Geom G, Phys P) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int c = blockIdx.z;
+  if (x >= G.Nx || y >= G.Ny) return;
+  const int pn = (c % 25) / 5, qn = c % 5;
+  const int sx = sgn_of(pn), sy = sgn_of(qn);
+  if (sx == 0 && sy == 0) return;
+  const long long off = cell_index(G, y, x) + (long long)c * G.plane;
+  const double* xc = X + off;
+  const double* lc = Lin + off;
+  double v = Lout[off];
+  if (RAT) {
+    if (sx != 0) v = fma(-P.kxr[pn], advection_adjoint_rat(xc, lc, 1, P.lp, P.lq, sx), v);
+    if (sy != 0) v = fma(-P.kyr[qn], advection_adjoint_rat(xc, lc, G.pitch, P.lp, P.lq, sy), v);
+  } else {
+    if (sx != 0) v = fma(-P.kxv[pn], advection_adjoint(xc, lc, 1, P.hq, sx), v);
+    if (sy != 0) v = fma(-P.kyv[qn], advection_adjoint(xc, lc, G.pitch, P.hq, sy), v);
+  }
+  Lout[off] = v;
 }
 
 // lambda^N from dL/drho and dL/dT of the final state; partial: gm1 adjoint
@@ -554,9 +628,14 @@ int adjoint_blocks(const Geom& G) { return ((G.Nx + 31) / 32) * ((G.Ny + 7) / 8)
 cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial, const Geom& G,
                                 const Phys& P, cudaStream_t st) {
   dim3 block(32, 8), grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
-  if (P.prc < 0) k_adjoint_step<-1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
-  else if (P.prc > 0) k_adjoint_step<1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
-  else k_adjoint_step<0><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  if (P.prc < 0) k_adjoint_local<-1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  else if (P.prc > 0) k_adjoint_local<1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  else k_adjoint_local<0><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grid3(grid.x, grid.y, NPOP);
+  if (P.lq > 0) k_adjoint_adv<true><<<grid3, block, 0, st>>>(X, Lin, Lout, G, P);
+  else k_adjoint_adv<false><<<grid3, block, 0, st>>>(X, Lin, Lout, G, P);
   return cudaGetLastError();
 }
 

@@ -87,6 +87,10 @@ static void set_step_factors(dvbm_ctx* c) {
     c->P.kxv[k] = c->dt / dx * c->M.c * xi_of(k);
     c->P.kyv[k] = c->dt / dy * c->M.c * xi_of(k);
     c->P.kxvf[k] = (float)c->P.kxv[k];
+    if (c->P.lq > 0) {
+      c->P.kxr[k] = c->P.kxv[k] / (4.0 * c->P.lq);
+      c->P.kyr[k] = c->P.kyv[k] / (4.0 * c->P.lq);
+    }
     c->P.kyvf[k] = (float)c->P.kyv[k];
   }
   c->P.dt = c->dt;
@@ -148,6 +152,16 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
   c->P.prc = Pr < 1.0 ? -1 : (Pr > 1.0 ? 1 : 0);
   c->P.hb = 0.5 * o.beta;
   c->P.hq = (long long)std::llround(std::ldexp(0.5 * o.beta, 62));
+  c->P.lp = 0;
+  c->P.lq = 0;
+  for (int q = 1; q <= 64; ++q) {  // beta = lp / lq exactly (to double precision)?
+    const double pq = o.beta * q;
+    if (std::fabs(pq - std::nearbyint(pq)) < 1e-12 * pq) {
+      c->P.lp = (int)std::nearbyint(pq);
+      c->P.lq = q;
+      break;
+    }
+  }
   c->P.fref0 = o.rho0;
   c->P.gref0 = o.rho0 * (o.R / (gamma - 1.0) - o.R) * o.T0;
   for (int s = 0; s < 4; ++s) {

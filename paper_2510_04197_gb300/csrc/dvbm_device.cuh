@@ -59,7 +59,9 @@ struct Phys {
   double dt_mu;          // dt / mu
   int prc;               // -1: Pr < 1, 0: Pr == 1, +1: Pr > 1
   double hb;             // beta / 2
-  long long hq;          // round(beta/2 * 2^62), integer-pipe limiter
+  long long hq;          // round(beta/2 * 2^62), integer-pipe limiter (general beta)
+  int lp, lq;            // beta = lp / lq exactly (lq <= 64), or lq = 0: use hq
+  double kxr[5], kyr[5]; // kxv / (4 lq), kyv / (4 lq): flux factors of the scaled differences
   double kxv[5], kyv[5]; // dt/dx * c * xi_k and dt/dy * c * xi_k
   float kxvf[5], kyvf[5];
   double fref0, gref0;   // FP32DEV reference: f_ref = w rho0, g_ref = w rho0 (C_v - R) T0
@@ -373,11 +375,25 @@ __device__ __forceinline__ long long to_block_fixed(double v, int E) {
   return hi < 0 ? -(long long)mag : (long long)mag;
 }
 
-// value of integer F at block exponent E: F 2^(E - 1075 - 7)
+// int64 -> double by bit manipulation (the hardware conversion runs at the FP64
+// rate on GB300): |F| is normalised with a count of leading zeros, its top 53
+// bits become the significand (truncating the rest, < 2^-52 relative), and
+// the exponent is that of F times 2^scale.  F = 0 gives 0.
+__device__ __forceinline__ double ll_to_double_scaled(long long F, int scale) {
+  if (F == 0) return 0.0;
+  const unsigned long long mag = F < 0 ? (unsigned long long)(-F) : (unsigned long long)F;
+  const int lz = __clzll(mag);
+  const unsigned long long norm = mag << lz;           // leading one at bit 63
+  const unsigned long long frac = (norm >> 11) & 0x000fffffffffffffull;
+  const int ex = 1023 + 63 - lz + scale;
+  const unsigned hi = (unsigned)(frac >> 32) | ((unsigned)ex << 20) | (F < 0 ? 0x80000000u : 0u);
+  return __hiloint2double((int)hi, (int)(unsigned)frac);
+}
+
+// value of integer F at block exponent E: F 2^(E - 1082)
 __device__ __forceinline__ double from_block_fixed(long long F, int E) {
-  if (F == 0 || E < 64) return 0.0;
-  const double d = __ll2double_rn(F);
-  return __hiloint2double(__double2hiint(d) + ((E - 1082) << 20), __double2loint(d));
+  if (E < 64) return 0.0;
+  return ll_to_double_scaled(F, E - 1082);
 }
 
 // limited slope on integers: minmod3(hb Da, (Da + Db)/4, hb Db); Hq = hb 2^62
@@ -404,6 +420,38 @@ __device__ __forceinline__ double flux_difference_int(const double* __restrict__
   // v < 0 (cells j-1..j+2): dF = D_{j+1} - sigma_{j+1} + sigma_j = Db - s_bc + s_ab
   const long long F = sgn > 0 ? Db + s_bc - s_ab : Db - s_bc + s_ab;
   return from_block_fixed(F, E);
+}
+
+
+// Rational limiter: with beta = lp/lq the scaled slope 4 lq sigma equals
+// minmod3(2 lp Da, lq (Da + Db), 2 lp Db) exactly, so the flux difference
+// scaled by 4 lq needs only small-integer multiplies.  Values enter with a
+// 52-bit significand (X = value 2^(1074 - E)) to leave headroom for the
+// factors (lp <= 128, lq <= 64).
+__device__ __forceinline__ long long slope_rat(long long Da, long long Db, long long lp2, long long lq) {
+  const long long ra = lp2 * Da, rb = lp2 * Db, y = lq * (Da + Db);
+  const long long mn = min(min(ra, y), rb), mx = max(max(ra, y), rb);
+  return ((Da ^ Db) >= 0) ? (Da >= 0 ? mn : mx) : 0ll;
+}
+
+__device__ __forceinline__ long long to_block_fixed52(double v, int E) { return to_block_fixed(v, E) >> 8; }
+
+// returns 4 lq (F_{j+1/2} - F_{j-1/2}) as a double (the caller folds 1/(4 lq))
+__device__ __forceinline__ double flux_difference_rat(const double* __restrict__ ptr, long long stride, int lp,
+                                                      int lq, int sgn) {
+  const long long o0 = sgn > 0 ? -2 * stride : -stride;
+  const double a0 = __ldg(ptr + o0), a1 = __ldg(ptr + o0 + stride), a2 = __ldg(ptr + o0 + 2 * stride),
+               a3 = __ldg(ptr + o0 + 3 * stride);
+  const int E = max(max(bexp(a0), bexp(a1)), max(bexp(a2), bexp(a3)));
+  const long long x0 = to_block_fixed52(a0, E), x1 = to_block_fixed52(a1, E), x2 = to_block_fixed52(a2, E),
+                  x3 = to_block_fixed52(a3, E);
+  const long long Da = x1 - x0, Db = x2 - x1, Dc = x3 - x2;
+  const long long lp2 = 2 * lp, q4 = 4 * lq;
+  const long long s_ab = slope_rat(Da, Db, lp2, lq);
+  const long long s_bc = slope_rat(Db, Dc, lp2, lq);
+  const long long F = sgn > 0 ? q4 * Db + s_bc - s_ab : q4 * Db - s_bc + s_ab;
+  if (E < 64) return 0.0;
+  return ll_to_double_scaled(F, E - 1074);  // value = F 2^(E - 1074)
 }
 
 template <int SGN, class T>

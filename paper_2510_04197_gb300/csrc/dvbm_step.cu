@@ -37,7 +37,7 @@ __device__ __forceinline__ void load_node(const S* __restrict__ src, long long p
   }
 }
 
-template <class S, int PRC>
+template <class S, int PRC, bool RAT>
 __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
                                               unsigned int* __restrict__ flag) {
   const int x = blockIdx.x * 32 + threadIdx.x;
@@ -65,15 +65,21 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
     m.m00 += P.fref0; m.m20 += P.fref0; m.m02 += P.fref0;
     m.g00 += P.gref0;
   }
-  const Coeffs C = collision_coeffs<PRC>(m, P);
+  Coeffs C = collision_coeffs<PRC>(m, P);
   if (C.bad) atomicOr(flag, 1u);
+  if constexpr (sizeof(S) == 4) {
+    // the expansion then yields t - (dt/tau1) F_ref directly: the reference
+    // populations w rho0 and w G0 have only a zeroth Hermite coefficient
+    C.f00 -= C.k1 * P.fref0;
+    C.g00 -= C.k1 * P.gref0;
+  }
 
   typedef typename StoreT<S>::adv_t A;
   const A hb = (A)P.hb;
   // FP32DEV: new deviation = a1 * dev + (t - k1 * ref) - advection, with the
   // bracket (equilibrium evaluation minus the relaxed reference) in double
-  const double kref_f = -C.k1 * P.fref0, kref_g = -C.k1 * P.gref0;
   const float a1f = (float)C.a1;
+  constexpr bool rational = RAT;
 
   // ---- phase B: populations, x-node by x-node ----
 #define DVBM_NODE(p)                                                                       \
@@ -88,8 +94,13 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
         const double t = k == 0 ? tf[q] : tg[q];                                            \
         A fx = 0, fy = 0;                                                                   \
         if constexpr (sizeof(S) == 8) {                                                     \
-          if (sgn_of(p) != 0) fx = flux_difference_int((const double*)pc, 1, P.hq, sgn_of(p)); \
-          if (sgn_of(q) != 0) fy = flux_difference_int((const double*)pc, PT, P.hq, sgn_of(q)); \
+          if constexpr (rational) {                                                         \
+            if (sgn_of(p) != 0) fx = flux_difference_rat((const double*)pc, 1, P.lp, P.lq, sgn_of(p));   \
+            if (sgn_of(q) != 0) fy = flux_difference_rat((const double*)pc, PT, P.lp, P.lq, sgn_of(q));  \
+          } else {                                                                          \
+            if (sgn_of(p) != 0) fx = flux_difference_int((const double*)pc, 1, P.hq, sgn_of(p)); \
+            if (sgn_of(q) != 0) fy = flux_difference_int((const double*)pc, PT, P.hq, sgn_of(q)); \
+          }                                                                                 \
         } else {                                                                            \
           if (sgn_of(p) > 0) fx = flux_difference<1, S>(pc, 1, (S)hb);                      \
           if (sgn_of(p) < 0) fx = flux_difference<-1, S>(pc, 1, (S)hb);                     \
@@ -98,11 +109,11 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
         }                                                                                   \
         if constexpr (sizeof(S) == 8) {                                                     \
           double v = fma(C.a1, (double)__ldg(pc), t);                                       \
-          if (sgn_of(p) != 0) v = fma(-P.kxv[p], (double)fx, v);                            \
-          if (sgn_of(q) != 0) v = fma(-P.kyv[q], (double)fy, v);                            \
+          if (sgn_of(p) != 0) v = fma(rational ? -P.kxr[p] : -P.kxv[p], (double)fx, v);    \
+          if (sgn_of(q) != 0) v = fma(rational ? -P.kyr[q] : -P.kyv[q], (double)fy, v);    \
           d[c * PL] = (S)v;                                                                 \
         } else {                                                                            \
-          const double base = fma(k == 0 ? kref_f : kref_g, w_of(p) * w_of(q), t);         \
+          const double base = t;                                                            \
           float adv = 0.f;                                                                  \
           if (sgn_of(p) != 0) adv = P.kxvf[p] * (float)fx;                                  \
           if (sgn_of(q) != 0) adv = fmaf(P.kyvf[q], (float)fy, adv);                        \
@@ -126,9 +137,18 @@ static cudaError_t launch_step_t(const void* src, void* dst, const Geom& G, cons
   dim3 grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
   const S* s = (const S*)src;
   S* d = (S*)dst;
-  if (P.prc < 0) k_step<S, -1><<<grid, block, 0, st>>>(s, d, G, P, flag);
-  else if (P.prc > 0) k_step<S, 1><<<grid, block, 0, st>>>(s, d, G, P, flag);
-  else k_step<S, 0><<<grid, block, 0, st>>>(s, d, G, P, flag);
+  // the rational limiter form matters only for FP64 storage
+  const bool rat = sizeof(S) == 8 && P.lq > 0;
+  if (P.prc < 0) {
+    if (rat) k_step<S, -1, true><<<grid, block, 0, st>>>(s, d, G, P, flag);
+    else k_step<S, -1, false><<<grid, block, 0, st>>>(s, d, G, P, flag);
+  } else if (P.prc > 0) {
+    if (rat) k_step<S, 1, true><<<grid, block, 0, st>>>(s, d, G, P, flag);
+    else k_step<S, 1, false><<<grid, block, 0, st>>>(s, d, G, P, flag);
+  } else {
+    if (rat) k_step<S, 0, true><<<grid, block, 0, st>>>(s, d, G, P, flag);
+    else k_step<S, 0, false><<<grid, block, 0, st>>>(s, d, G, P, flag);
+  }
   return cudaGetLastError();
 }
 

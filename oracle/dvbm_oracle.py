@@ -9,15 +9,17 @@ What it computes (Strässle, Hosseini & Karlin, "Consistent kinetic modeling of
 compressible flows with variable Prandtl numbers: double-distribution
 quasi-equilibrium approach"):
 
-* the D2Q25 Gauss--Hermite lattice (App. G, Table "D2Q25"),
+* the D2Q25 and D2Q16 Gauss--Hermite lattices (App. G, Tables "D2Q25" and
+  "D2Q16"),
 * moments of the populations (Sec. II.D.1, Eqs. eq_quadratur1-3) with the
-  internal non-translational energy split (II), temperature from the total
-  energy (Eq. Total_energy_MB),
+  internal non-translational energy split (II, on D2Q25) or the total energy
+  split (I, on D2Q16), temperature from the total energy
+  (Eq. Total_energy_MB),
 * relaxation times from mu and Pr (Sec. II.C, Eqs. visc_shear_1/2,
   Pr_times_cases),
 * Grad--Hermite equilibria (Sec. II.D.2, Eq. Grad_g; App. D) for f to fourth
   order and g to second order (Sec. II.D.3, App. E),
-* quasi-equilibria from the moment sets of Table I (split II rows) converted to
+* quasi-equilibria from the moment sets of Table I (split I and II rows) converted to
   Hermite coefficients with the semi-recursive formulas (App. D,
   Eq. Hermitecoefficients-static-regform),
 * the explicit finite-volume update (Sec. III.A.1, Eq. finalDiscretePDE) with
@@ -57,37 +59,52 @@ D = 2  # physical dimension
 
 
 class Lattice:
-    """D2Q25 tensor-product Gauss--Hermite velocity set.
+    """Tensor-product Gauss--Hermite velocity sets of App. G.
 
-    App. G, Table "D2Q25 (Hermite) for T_ref = 1": the five 1-D abscissae are
-    0, +-sqrt(5 - sqrt(10)), +-sqrt(5 + sqrt(10)) (roots of He_5) and the 2-D
-    weights are products of 1-D weights.  The table prints the 1-D weights as
-    8/15 and (7 +- 2 sqrt(10)) without their common denominator; the 1-D
-    Gauss--Hermite weights of He_5 are 8/15 and (7 +- 2 sqrt(10))/60 (they sum
-    to one).  Velocities scale with sqrt(R T_ref).
+    D2Q25 (Table "D2Q25 (Hermite) for T_ref = 1", used with split II): the
+    five 1-D abscissae are 0, +-sqrt(5 - sqrt(10)), +-sqrt(5 + sqrt(10)) (roots
+    of He_5).  The table prints the 1-D weights as 8/15 and (7 +- 2 sqrt(10))
+    without their common denominator; the 1-D Gauss--Hermite weights of He_5
+    are 8/15 and (7 +- 2 sqrt(10))/60 (they sum to one).
 
-    The oracle's own population order: x-node index p over ascending
-    abscissae, y-node index q likewise, population i = 5 p + q.
+    D2Q16 (Table "D2Q16 (Hermite) for T_ref = 1", used with split I): 1-D
+    abscissae +-sqrt(3 - sqrt(6)), +-sqrt(3 + sqrt(6)) (roots of He_4) with
+    weights (3 + sqrt(6))/12 and (3 - sqrt(6))/12.
+
+    2-D weights are products of 1-D weights; velocities scale with
+    sqrt(R T_ref).  The oracle's own population order: x-node index p over
+    ascending abscissae, y-node index q likewise, population i = n p + q.
     """
 
-    def __init__(self, R: float = 1.0, T_ref: float = 1.0):
-        s10 = math.sqrt(10.0)
-        a1 = math.sqrt(5.0 - s10)
-        a2 = math.sqrt(5.0 + s10)
-        xi = [-a2, -a1, 0.0, a1, a2]
-        w1 = [(7.0 - 2.0 * s10) / 60.0, (7.0 + 2.0 * s10) / 60.0, 8.0 / 15.0,
-              (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0]
+    def __init__(self, R: float = 1.0, T_ref: float = 1.0, kind: str = "D2Q25"):
+        if kind == "D2Q25":
+            s10 = math.sqrt(10.0)
+            a1 = math.sqrt(5.0 - s10)
+            a2 = math.sqrt(5.0 + s10)
+            xi = [-a2, -a1, 0.0, a1, a2]
+            w1 = [(7.0 - 2.0 * s10) / 60.0, (7.0 + 2.0 * s10) / 60.0, 8.0 / 15.0,
+                  (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0]
+        elif kind == "D2Q16":
+            s6 = math.sqrt(6.0)
+            a1 = math.sqrt(3.0 - s6)
+            a2 = math.sqrt(3.0 + s6)
+            xi = [-a2, -a1, a1, a2]
+            w1 = [(3.0 - s6) / 12.0, (3.0 + s6) / 12.0, (3.0 + s6) / 12.0, (3.0 - s6) / 12.0]
+        else:
+            raise ValueError(kind)
+        self.kind = kind
         self.R = float(R)
         self.T_ref = float(T_ref)
         self.c2 = self.R * self.T_ref  # R T_ref, the Hermite scale
         c = math.sqrt(self.c2)
+        n = len(xi)
         vx, vy, w = [], [], []
-        for p in range(5):
-            for q in range(5):
+        for p in range(n):
+            for q in range(n):
                 vx.append(c * xi[p])
                 vy.append(c * xi[q])
                 w.append(w1[p] * w1[q])
-        self.Q = 25
+        self.Q = n * n
         self.vx = torch.tensor(vx, dtype=DT)
         self.vy = torch.tensor(vy, dtype=DT)
         self.w = torch.tensor(w, dtype=DT)
@@ -164,19 +181,23 @@ class Params:
     R: float = 1.0
     T_ref: float = 1.0
     beta: float = 1.2  # limiter parameter, Sec. III.A.3
+    split: str = "II"  # energy split: "I" total energy on g, "II" internal non-translational (Sec. II.B.3)
 
     def Cv(self):
         return self.R / (self.gamma - 1.0)
 
 
 def macroscopic(lat: Lattice, P: Params, f: torch.Tensor, g: torch.Tensor):
-    """rho, rho u, E (split II) and T (Sec. II.D.1 Eqs. eq_quadratur1-3;
-    Eq. Total_energy_MB: E = rho C_v T + rho u^2 / 2)."""
+    """rho, rho u, E and T (Sec. II.D.1 Eqs. eq_quadratur1-3: E = sum g (I) or
+    sum g + v^2/2 f (II); Eq. Total_energy_MB: E = rho C_v T + rho u^2 / 2)."""
     rho = f.sum(0)
     jx = torch.einsum("i,i...->...", lat.vx, f)
     jy = torch.einsum("i,i...->...", lat.vy, f)
     v2 = lat.vx * lat.vx + lat.vy * lat.vy
-    E = g.sum(0) + torch.einsum("i,i...->...", 0.5 * v2, f)
+    if P.split == "I":
+        E = g.sum(0)
+    else:
+        E = g.sum(0) + torch.einsum("i,i...->...", 0.5 * v2, f)
     ux = jx / rho
     uy = jy / rho
     T = (E / rho - 0.5 * (ux * ux + uy * uy)) / P.Cv()
@@ -252,11 +273,26 @@ def maxwell_moment(lat: Lattice, R: float, rho, u, T, tup):
 
 
 def g_eq_moment(P: Params, rho, u, T, tup):
-    """Equilibrium moments of g for split II (App. A):
+    """Equilibrium moments of g.  Split I (App. A, Eqs. Relevantmoments_E, _q,
+    _R with g alone): int g^eq = E = rho (C_v T + u^2/2),
+    int v_a g^eq = u_a (E + rho R T),
+    int v_a v_b g^eq = rho R T u_a u_b + (E + rho R T)(u_a u_b + R T d_ab).
+    Split II (App. A):
     int g^eq = rho (C_v T - R T D/2), int v_a g^eq = rho (C_v T - R T D/2) u_a,
     int v_a v_b g^eq = rho (C_v T - R T D/2)(u_a u_b + R T d_ab)."""
-    eps = P.Cv() * T - P.R * T * D / 2.0
     n = len(tup)
+    if P.split == "I":
+        RT = P.R * T
+        E = rho * (P.Cv() * T + 0.5 * (u[0] * u[0] + u[1] * u[1]))
+        if n == 0:
+            return E
+        if n == 1:
+            return u[tup[0]] * (E + rho * RT)
+        if n == 2:
+            uu = u[tup[0]] * u[tup[1]]
+            return rho * RT * uu + (E + rho * RT) * (uu + RT * _delta(tup[0], tup[1]))
+        raise ValueError
+    eps = P.Cv() * T - P.R * T * D / 2.0
     if n == 0:
         return rho * eps
     if n == 1:
@@ -316,13 +352,19 @@ def grad_expansion(lat: Lattice, a: dict, N: int) -> torch.Tensor:
 # ---------------------------------------------------------------------------
 
 
+def f_order(P: Params) -> int:
+    """Expansion order of f (Sec. II.D.3, App. E): N_f = 3 for split I, 4 for
+    split II; g is expanded to N_g = 2 for both."""
+    return 3 if P.split == "I" else 4
+
+
 def equilibria(lat: Lattice, P: Params, rho, ux, uy, T):
-    """f^eq (N = 4, theta-form coefficients) and g^eq (N = 2, coefficients from
-    the g^eq moments through the semi-recursive formulas).  Orders from
-    Sec. II.D.3 / App. E for split II."""
+    """f^eq (N_f, theta-form coefficients) and g^eq (N = 2, coefficients from
+    the g^eq moments through the semi-recursive formulas)."""
     u = (ux, uy)
-    af = {t: a_eq_f(lat, rho, u, T, t) for n in range(5) for t in tuples(n)}
-    feq = grad_expansion(lat, af, 4)
+    Nf = f_order(P)
+    af = {t: a_eq_f(lat, rho, u, T, t) for n in range(Nf + 1) for t in tuples(n)}
+    feq = grad_expansion(lat, af, Nf)
     Mg = {t: g_eq_moment(P, rho, u, T, t) for n in range(3) for t in tuples(n)}
     ag = coefficients_from_moments(lat, Mg, 2)
     geq = grad_expansion(lat, ag, 2)
@@ -356,10 +398,12 @@ def quasi_equilibria(lat: Lattice, P: Params, f, g, rho, ux, uy, T, feq, geq):
     Moments M_n(.) are lattice sums (Table I notation); target moments are
     converted to Hermite coefficients with the semi-recursive formulas.
     """
-    Pr = float(P.Pr)
+    Pr = float(P.Pr.detach() if torch.is_tensor(P.Pr) else P.Pr)
     if Pr == 1.0:
         return feq, geq
     u = (ux, uy)
+    if P.split == "I":
+        return _quasi_equilibria_split_I(lat, P, f, g, u, feq, geq, Pr)
     Mf = {t: lattice_moment(lat, f, t) for n in range(4) for t in tuples(n)}
     Meq = {t: lattice_moment(lat, feq, t) for n in range(5) for t in tuples(n)}
     Delta = {t: Mf[t] - Meq[t] for t in tuples(2)}
@@ -391,6 +435,36 @@ def quasi_equilibria(lat: Lattice, P: Params, f, g, rho, ux, uy, T, feq, geq):
         gstar = grad_expansion(lat, ag, 2)
     else:
         gstar = geq
+    return fstar, gstar
+
+
+def _quasi_equilibria_split_I(lat, P, f, g, u, feq, geq, Pr):
+    """Table I, total energy split (I):
+    Pr < 1: f* = f^eq; g* keeps M_0, M_2 of g^eq and takes
+            M_1(g) - u . (M_2(f) - M_2(f^eq)).
+    Pr > 1: f* takes M_2(f) and keeps M_0, M_1, M_3 of f^eq; g* keeps M_0, M_2
+            of g^eq and takes M_1(g^eq) + u . (M_2(f) - M_2(f^eq)).
+    (u . A)_a = u_b A_ba."""
+    Nf = f_order(P)
+    Mf2 = {t: lattice_moment(lat, f, t) for t in tuples(2)}
+    Meq = {t: lattice_moment(lat, feq, t) for n in range(Nf + 1) for t in tuples(n)}
+    Delta = {t: Mf2[t] - Meq[t] for t in tuples(2)}
+    if Pr < 1.0:
+        fstar = feq
+        M1g = {t: lattice_moment(lat, g, t) for t in tuples(1)}
+        sign = -1.0
+    else:
+        Mstar = dict(Meq)
+        for t in tuples(2):
+            Mstar[t] = Mf2[t]
+        fstar = grad_expansion(lat, coefficients_from_moments(lat, Mstar, Nf), Nf)
+        M1g = {t: lattice_moment(lat, geq, t) for t in tuples(1)}
+        sign = 1.0
+    Mg = {t: lattice_moment(lat, geq, t) for n in (0, 2) for t in tuples(n)}
+    for t in tuples(1):
+        a = t[0]
+        Mg[t] = M1g[t] + sign * (u[0] * Delta[(0, a)] + u[1] * Delta[(1, a)])
+    gstar = grad_expansion(lat, coefficients_from_moments(lat, Mg, 2), 2)
     return fstar, gstar
 
 
@@ -627,7 +701,7 @@ class Simulation:
     """Convenience driver: equilibrium ICs, fixed dt, n steps, moments."""
 
     def __init__(self, grid: Grid, P: Params, rho, ux, uy, T, cfl=0.01, dt=None):
-        self.lat = Lattice(P.R, P.T_ref)
+        self.lat = Lattice(P.R, P.T_ref, "D2Q16" if P.split == "I" else "D2Q25")
         self.P = P
         self.grid = grid
         self.f, self.g = init_populations(self.lat, P, rho, ux, uy, T)

@@ -27,6 +27,10 @@ DT = torch.float64
 
 
 def run_modes(Pr, gamma, Ma, Nx=32, Ny=2, mu=0.01, dt=2e-4, n1=600, n2=1000, amp=1e-4):
+    return run_modes_split(Pr, gamma, Ma, Nx, Ny, mu, dt, n1, n2, amp, split="II")
+
+
+def run_modes_split(Pr, gamma, Ma, Nx=32, Ny=2, mu=0.01, dt=2e-4, n1=600, n2=1000, amp=1e-4, split="II"):
     x = (np.arange(Nx) + 0.5) / Nx
     rho = 1 + amp * np.sin(2 * np.pi * x)[None, :] + np.zeros((Ny, 1))
     T = 1 / rho
@@ -34,7 +38,7 @@ def run_modes(Pr, gamma, Ma, Nx=32, Ny=2, mu=0.01, dt=2e-4, n1=600, n2=1000, amp
     ux = np.full((Ny, Nx), u0)
     uy = amp * np.sin(2 * np.pi * x)[None, :] + np.zeros((Ny, 1))
     t = lambda a: torch.tensor(a, dtype=DT)
-    P = O.Params(Pr=Pr, gamma=gamma, mu=mu)
+    P = O.Params(Pr=Pr, gamma=gamma, mu=mu, split=split)
     s = O.Simulation(O.Grid(Nx, Ny, 1.0, Ny / Nx), P, t(rho), t(ux), t(uy), t(T), dt=dt)
     e = np.exp(-2j * np.pi * x)
 

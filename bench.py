@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL = {"fp64": 2 * 50 * 8, "fp32dev": 2 * 50 * 4}  # read + write all populations
+BYTES_PER_CELL = {"fp64": 2 * 50 * 8, "fp32dev": 2 * 50 * 4, "d2q16": 2 * 32 * 8}  # read + write all populations
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=512, help="oracle sample grid size")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-d2q16", action="store_true")
     return ap.parse_args()
 
 
@@ -268,8 +269,10 @@ def main():
     peaks, peak_kind = load_peaks()
     results = {}
     clocks = None
-    for storage in (["fp64"] if args.no_fp32dev else ["fp64", "fp32dev"]):
-        sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, storage=0 if storage == "fp64" else 1, check_every=-1)
+    variants = ["fp64"] + ([] if args.no_fp32dev else ["fp32dev"]) + ([] if args.no_d2q16 else ["d2q16"])
+    for storage in variants:
+        sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, storage=1 if storage == "fp32dev" else 0, check_every=-1,
+                              lattice=dvbm.D2Q16_SPLIT_I if storage == "d2q16" else dvbm.D2Q25_SPLIT_II)
         sim.init(*fields)
         sim.step(args.warmup)
         torch.cuda.synchronize()
@@ -357,6 +360,13 @@ def main():
                            "dtype": "f32 storage / f64 moments+equilibria",
                            "roofline_hbm": {"bound": "hbm", "achieved": g32, "peak": hbm_peak, "unit": "GB/s",
                                             "frac": g32 / hbm_peak}}
+    if "d2q16" in results:
+        r16 = results["d2q16"]
+        g16 = BYTES_PER_CELL["d2q16"] * N * N / (r16["kernel_ms"] * 1e-3) / 1e9
+        line["d2q16_split_I"] = {"value": r16["mlups"], "unit": "MLUPS", "ms_per_step": r16["ms_per_step"],
+                                 "dtype": "f64", "workload": "same flow, total-energy split (I) on D2Q16",
+                                 "roofline_hbm": {"bound": "hbm", "achieved": g16, "peak": hbm_peak, "unit": "GB/s",
+                                                  "frac": g16 / hbm_peak}}
     line["e2e"] = e2e
     if not args.no_adjoint:
         line["adjoint"] = adjoint_ratio(dvbm, inputs, torch)

@@ -47,8 +47,11 @@ typedef enum {
   DVBM_ESTATE = 6     /* call not valid in the context's current state */
 } dvbm_status;
 
-/* Lattice / energy split.  Only D2Q25 with split II is built. */
-typedef enum { DVBM_D2Q25_SPLIT_II = 0 } dvbm_lattice;
+/* Lattice / energy split (Sec. II.D.3, App. G): D2Q25 with the internal
+ * non-translational energy split (II; N_f = 4, N_g = 2; 50 planes) or D2Q16
+ * with the total energy split (I; E = sum g, N_f = 3, N_g = 2, Table I split-I
+ * quasi-equilibria; 32 planes; FP64 storage only, no adjoint). */
+typedef enum { DVBM_D2Q25_SPLIT_II = 0, DVBM_D2Q16_SPLIT_I = 1 } dvbm_lattice;
 
 /* Population storage.  FP64: populations as doubles.  FP32DEV: populations
  * stored as float deviations from w_i rho0 (f) and w_i rho0 (C_v - R) T0 (g);
@@ -124,12 +127,14 @@ dvbm_status dvbm_moments(dvbm_ctx* ctx, double* rho, double* ux, double* uy, dou
  * (sum over cells times dx dy).  Synchronous. */
 dvbm_status dvbm_totals(dvbm_ctx* ctx, double out[4]);
 
-/* Size in bytes of a state snapshot: 50 planes [c][Ny][Nx] of the storage
- * type (double for FP64, float deviations for FP32DEV) plus one 8-byte step
- * counter at the end.  Population order c = 5 p + q for f (c < 25) and
- * 25 + 5 p + q for g, with x-node p and y-node q in the order
- * (0, +sqrt(5 - sqrt 10), -sqrt(5 - sqrt 10), +sqrt(5 + sqrt 10), -sqrt(5 + sqrt 10))
- * times sqrt(R T_ref). */
+/* Size in bytes of a state snapshot: the population planes [c][Ny][Nx] of the
+ * storage type (double for FP64, float deviations for FP32DEV) plus one
+ * 8-byte step counter at the end.  D2Q25: 50 planes, c = 5 p + q for f
+ * (c < 25) and 25 + 5 p + q for g, x-node p and y-node q in the order
+ * (0, +sqrt(5 - sqrt 10), -sqrt(5 - sqrt 10), +sqrt(5 + sqrt 10), -sqrt(5 + sqrt 10));
+ * D2Q16: 32 planes, c = 4 p + q (f) and 16 + 4 p + q (g), node order
+ * (+sqrt(3 - sqrt 6), -sqrt(3 - sqrt 6), +sqrt(3 + sqrt 6), -sqrt(3 + sqrt 6));
+ * nodes times sqrt(R T_ref). */
 size_t dvbm_state_bytes(const dvbm_ctx* ctx);
 
 /* Copy the current state out / in (checkpoint / resume).  bytes must equal

@@ -13,7 +13,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdvbm.so")
-SOURCES = ["dvbm_step.cu", "dvbm_aux.cu", "dvbm_api.cu", "dvbm_noalloc.cu", "dvbm_adjoint.cu"]
+SOURCES = ["dvbm_step.cu", "dvbm_aux.cu", "dvbm_api.cu", "dvbm_noalloc.cu", "dvbm_adjoint.cu", "dvbm_d2q16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

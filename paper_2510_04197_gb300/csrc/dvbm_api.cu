@@ -16,6 +16,8 @@ using namespace dvbm;
 
 struct dvbm_ctx {
   int Nx = 0, Ny = 0, storage = 0;
+  int lattice = 0;
+  int npop = 50;
   double Pr = 0, gamma = 0, mu = 0;
   dvbm_opts opts{};
   dvbm_bc bcs[4]{};
@@ -81,11 +83,22 @@ extern "C" dvbm_status dvbm_default_opts(dvbm_opts* o) {
   return DVBM_OK;
 }
 
+// 1-D node k of the context's lattice (D2Q25: 0, +-sqrt(5 -+ sqrt 10);
+// D2Q16: +-sqrt(3 -+ sqrt 6), in the ABI order)
+static double node(const dvbm_ctx* c, int k) {
+  if (c->lattice == DVBM_D2Q16_SPLIT_I) {
+    const double a = std::sqrt(3.0 - std::sqrt(6.0)), b = std::sqrt(3.0 + std::sqrt(6.0));
+    const double v[4] = {a, -a, b, -b};
+    return k < 4 ? v[k] : 0.0;
+  }
+  return xi_of(k);
+}
+
 static void set_step_factors(dvbm_ctx* c) {
   const double dx = c->opts.Lx / c->Nx, dy = c->opts.Ly / c->Ny;
   for (int k = 0; k < 5; ++k) {
-    c->P.kxv[k] = c->dt / dx * c->M.c * xi_of(k);
-    c->P.kyv[k] = c->dt / dy * c->M.c * xi_of(k);
+    c->P.kxv[k] = c->dt / dx * c->M.c * node(c, k);
+    c->P.kyv[k] = c->dt / dy * c->M.c * node(c, k);
     c->P.kxvf[k] = (float)c->P.kxv[k];
     if (c->P.lq > 0) {
       c->P.kxr[k] = c->P.kxv[k] / (4.0 * c->P.lq);
@@ -102,8 +115,11 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
                                    void* stream) {
   if (!out) return fail(nullptr, DVBM_EINVAL, "out is NULL");
   *out = nullptr;
-  if (lattice != DVBM_D2Q25_SPLIT_II) return fail(nullptr, DVBM_EINVAL, "unsupported lattice %d", lattice);
+  if (lattice != DVBM_D2Q25_SPLIT_II && lattice != DVBM_D2Q16_SPLIT_I)
+    return fail(nullptr, DVBM_EINVAL, "unsupported lattice %d", lattice);
   if (storage != DVBM_FP64 && storage != DVBM_FP32DEV) return fail(nullptr, DVBM_EINVAL, "bad storage %d", storage);
+  if (lattice == DVBM_D2Q16_SPLIT_I && storage != DVBM_FP64)
+    return fail(nullptr, DVBM_EINVAL, "the D2Q16 / split I lattice is built for FP64 storage");
   if (Nx < 4 || Ny < 4 || Nx > (1 << 20) || Ny > 65535 || (long long)Nx * Ny > (1ll << 31))
     return fail(nullptr, DVBM_EINVAL, "grid %d x %d out of range (4 <= N, Ny <= 65535)", Nx, Ny);
   if (!(Pr > 0) || !std::isfinite(Pr)) return fail(nullptr, DVBM_EINVAL, "Pr must be > 0");
@@ -132,6 +148,8 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
 
   dvbm_ctx* c = new dvbm_ctx();
   c->Nx = Nx; c->Ny = Ny; c->storage = storage;
+  c->lattice = lattice;
+  c->npop = lattice == DVBM_D2Q16_SPLIT_I ? 32 : NPOP;
   c->Pr = Pr; c->gamma = gamma; c->mu = mu;
   c->opts = o;
   for (int s = 0; s < 4; ++s) c->bcs[s] = b[s];
@@ -169,7 +187,7 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
     c->bc.uw[s][0] = b[s].u_wall[0]; c->bc.uw[s][1] = b[s].u_wall[1];
     c->bc.Tw[s] = b[s].T_wall;
   }
-  const size_t bytes = (size_t)NPOP * c->G.plane * c->elem;
+  const size_t bytes = (size_t)c->npop * c->G.plane * c->elem;
   c->state_bytes_dev = bytes;
   for (int k = 0; k < 2; ++k) {
     cudaError_t e = cudaMalloc(&c->buf[k], bytes);
@@ -227,8 +245,29 @@ static dvbm_status check_flag(dvbm_ctx* c) {
 }
 
 static dvbm_status fill_ghosts(dvbm_ctx* c, void* b) {
-  CUDA_TRY(c, launch_ghost(c->storage, b, c->G, c->P, c->M, c->bc, c->stream));
+  if (c->lattice == DVBM_D2Q16_SPLIT_I) CUDA_TRY(c, launch_ghost16(b, c->G, c->P, c->M, c->bc, c->stream));
+  else CUDA_TRY(c, launch_ghost(c->storage, b, c->G, c->P, c->M, c->bc, c->stream));
   return DVBM_OK;
+}
+
+// lattice dispatch of the per-step and diagnostic kernels
+static cudaError_t l_step(dvbm_ctx* c, const void* src, void* dst) {
+  return c->lattice == DVBM_D2Q16_SPLIT_I ? launch_step16(src, dst, c->G, c->P, c->flag, c->stream)
+                                          : launch_step(c->storage, src, dst, c->G, c->P, c->flag, c->stream);
+}
+static cudaError_t l_init(dvbm_ctx* c, void* dst, const double* const* F) {
+  return c->lattice == DVBM_D2Q16_SPLIT_I
+             ? launch_init16(dst, F[0], F[1], F[2], F[3], c->G, c->P, c->M, c->stream)
+             : launch_init(c->storage, dst, F[0], F[1], F[2], F[3], c->G, c->P, c->M, c->stream);
+}
+static cudaError_t l_moments(dvbm_ctx* c, const void* src, double* r, double* a, double* b, double* t) {
+  return c->lattice == DVBM_D2Q16_SPLIT_I ? launch_moments16(src, r, a, b, t, c->G, c->P, c->M, c->stream)
+                                          : launch_moments(c->storage, src, r, a, b, t, c->G, c->P, c->M, c->stream);
+}
+static cudaError_t l_totals(dvbm_ctx* c, const void* src) {
+  return c->lattice == DVBM_D2Q16_SPLIT_I
+             ? launch_totals16(src, c->partial, c->nred, c->G, c->P, c->M, c->stream)
+             : launch_totals(c->storage, src, c->partial, c->nred, c->G, c->P, c->M, c->stream);
 }
 
 // device copies of host field arrays (or pass-through for device pointers)
@@ -283,6 +322,8 @@ extern "C" dvbm_status dvbm_record(dvbm_ctx* c, int every) {
   if (!c) return DVBM_EINVAL;
   if (every < 0) return fail(c, DVBM_EINVAL, "record interval must be >= 0");
   if (every > 0 && c->storage != DVBM_FP64) return fail(c, DVBM_EINVAL, "the adjoint needs FP64 storage");
+  if (every > 0 && c->lattice != DVBM_D2Q25_SPLIT_II)
+    return fail(c, DVBM_EINVAL, "the adjoint is built for the D2Q25 / split II model");
   for (int s = 0; s < 4 && every > 0; ++s)
     if (c->bcs[s].kind != DVBM_BC_PERIODIC) return fail(c, DVBM_EINVAL, "the adjoint is built for periodic domains");
   clear_record(c);
@@ -311,7 +352,7 @@ extern "C" dvbm_status dvbm_init(dvbm_ctx* c, const double* rho, const double* u
   else c->dt = c->opts.cfl * std::fmin(c->opts.Lx / c->Nx, c->opts.Ly / c->Ny) / vmax;
   set_step_factors(c);
   c->cur = 0;
-  CUDA_TRY(c, launch_init(c->storage, c->buf[0], F.p[0], F.p[1], F.p[2], F.p[3], c->G, c->P, c->M, c->stream));
+  CUDA_TRY(c, l_init(c, c->buf[0], F.p));
   s = fill_ghosts(c, c->buf[0]);
   if (s != DVBM_OK) return s;
   CUDA_TRY(c, cudaMemsetAsync(c->flag, 0, sizeof(unsigned int), c->stream));
@@ -341,7 +382,7 @@ extern "C" dvbm_status dvbm_step(dvbm_ctx* c, int n) {
   for (int i = 0; i < n; ++i) {
     void* src = c->buf[c->cur];
     void* dst = c->buf[1 - c->cur];
-    CUDA_TRY(c, launch_step(c->storage, src, dst, c->G, c->P, c->flag, c->stream));
+    CUDA_TRY(c, l_step(c, src, dst));
     dvbm_status s = fill_ghosts(c, dst);
     if (s != DVBM_OK) return s;
     c->cur = 1 - c->cur;
@@ -365,13 +406,12 @@ extern "C" dvbm_status dvbm_moments(dvbm_ctx* c, double* rho, double* ux, double
   const size_t n = (size_t)c->Nx * c->Ny;
   double* outs[4] = {rho, ux, uy, T};
   if (on_device) {
-    CUDA_TRY(c, launch_moments(c->storage, c->buf[c->cur], rho, ux, uy, T, c->G, c->P, c->M, c->stream));
+    CUDA_TRY(c, l_moments(c, c->buf[c->cur], rho, ux, uy, T));
     return DVBM_OK;
   }
   double* tmp = nullptr;
   CUDA_TRY(c, cudaMalloc(&tmp, 4 * n * sizeof(double)));
-  cudaError_t e = launch_moments(c->storage, c->buf[c->cur], tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, c->G, c->P,
-                                 c->M, c->stream);
+  cudaError_t e = l_moments(c, c->buf[c->cur], tmp, tmp + n, tmp + 2 * n, tmp + 3 * n);
   for (int k = 0; k < 4 && e == cudaSuccess; ++k)
     if (outs[k]) e = cudaMemcpyAsync(outs[k], tmp + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   dvbm_status s = e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "moments: %s", cudaGetErrorString(e));
@@ -382,7 +422,7 @@ extern "C" dvbm_status dvbm_moments(dvbm_ctx* c, double* rho, double* ux, double
 extern "C" dvbm_status dvbm_totals(dvbm_ctx* c, double out[4]) {
   if (!c || !out) return DVBM_EINVAL;
   if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
-  CUDA_TRY(c, launch_totals(c->storage, c->buf[c->cur], c->partial, c->nred, c->G, c->P, c->M, c->stream));
+  CUDA_TRY(c, l_totals(c, c->buf[c->cur]));
   std::vector<double> h(6 * c->nred);
   CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   dvbm_status s = wait_stream(c);
@@ -398,7 +438,7 @@ extern "C" dvbm_status dvbm_totals(dvbm_ctx* c, double out[4]) {
 
 extern "C" size_t dvbm_state_bytes(const dvbm_ctx* c) {
   if (!c) return 0;
-  return (size_t)NPOP * c->Nx * c->Ny * c->elem + 8;
+  return (size_t)c->npop * c->Nx * c->Ny * c->elem + 8;
 }
 
 extern "C" dvbm_status dvbm_get_state(dvbm_ctx* c, void* buf, size_t bytes, int on_device) {
@@ -408,7 +448,7 @@ extern "C" dvbm_status dvbm_get_state(dvbm_ctx* c, void* buf, size_t bytes, int 
   const size_t pb = bytes - 8;
   void* dev = buf;
   if (!on_device) CUDA_TRY(c, cudaMalloc(&dev, pb));
-  cudaError_t e = launch_pack(c->storage, c->buf[c->cur], dev, 1, c->G, c->stream);
+  cudaError_t e = launch_pack(c->storage, c->buf[c->cur], dev, 1, c->G, c->npop, c->stream);
   if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(buf, dev, pb, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((char*)buf + pb, &c->steps, 8, on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
@@ -433,7 +473,7 @@ extern "C" dvbm_status dvbm_set_state(dvbm_ctx* c, const void* buf, size_t bytes
   }
   cudaError_t e = cudaSuccess;
   if (!on_device) e = cudaMemcpyAsync(dev, buf, pb, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = launch_pack(c->storage, c->buf[c->cur], dev, 0, c->G, c->stream);
+  if (e == cudaSuccess) e = launch_pack(c->storage, c->buf[c->cur], dev, 0, c->G, c->npop, c->stream);
   long long st = 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&st, (const char*)buf + pb, 8, on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,

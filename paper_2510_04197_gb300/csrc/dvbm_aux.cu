@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(256) k_speed(const double* __restrict__ rho, c
 
 template <class S>
 __global__ void k_pack(S* buf, S* packed, int to_packed, Geom G) {
+  // one plane per blockIdx.z
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   const int c = blockIdx.z;
@@ -236,8 +237,9 @@ cudaError_t launch_speed(const double* rho, const double* ux, const double* uy, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G, cudaStream_t st) {
-  dim3 b(128), g((G.Nx + 127) / 128, G.Ny, NPOP);
+cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G, int npop,
+                        cudaStream_t st) {
+  dim3 b(128), g((G.Nx + 127) / 128, G.Ny, npop);
   if (storage == 0) k_pack<double><<<g, b, 0, st>>>((double*)buf, (double*)packed, to_packed, G);
   else k_pack<float><<<g, b, 0, st>>>((float*)buf, (float*)packed, to_packed, G);
   return cudaGetLastError();

@@ -29,8 +29,20 @@ cudaError_t launch_totals(int storage, const void* src, double* partial, int nbl
 // per-block maxima of |u| + sqrt(gamma R T) and a bad-input count: out[blk*2 + {max, bad}]
 cudaError_t launch_speed(const double* rho, const double* ux, const double* uy, const double* T, long long n,
                          double* partial, int nblocks, const Macro& M, cudaStream_t st);
-cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G,
+cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G, int npop,
                         cudaStream_t st);
+
+// D2Q16, total-energy split (I), FP64 storage
+cudaError_t launch_step16(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
+                          cudaStream_t st);
+cudaError_t launch_init16(void* dst, const double* rho, const double* ux, const double* uy, const double* T,
+                          const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
+cudaError_t launch_moments16(const void* src, double* rho, double* ux, double* uy, double* T, const Geom& G,
+                             const Phys& P, const Macro& M, cudaStream_t st);
+cudaError_t launch_totals16(const void* src, double* partial, int nblocks, const Geom& G, const Phys& P,
+                            const Macro& M, cudaStream_t st);
+cudaError_t launch_ghost16(void* buf, const Geom& G, const Phys& P, const Macro& M, const BCDev& bc,
+                           cudaStream_t st);
 
 // adjoint (FP64 storage, periodic)
 int adjoint_blocks(const Geom& G);

@@ -18,7 +18,7 @@ LIBPATH = os.path.join(_HERE, "libdvbm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "ETIMEOUT", "ESTATE"]
-D2Q25_SPLIT_II = 0
+D2Q25_SPLIT_II, D2Q16_SPLIT_I = 0, 1
 FP64, FP32DEV = 0, 1
 PERIODIC, ZEROGRAD, WALL = 0, 1, 2
 XLO, XHI, YLO, YHI = 0, 1, 2, 3
@@ -124,15 +124,17 @@ class Simulation:
     """A DVBM context on the current CUDA device and torch's current stream."""
 
     def __init__(self, Nx: int, Ny: int, Pr: float, gamma: float, mu: float, bcs=None,
-                 storage: int = FP64, stream=None, **opts):
+                 storage: int = FP64, stream=None, lattice: int = D2Q25_SPLIT_II, **opts):
         torch = _torch()
         self.Nx, self.Ny, self.storage = int(Nx), int(Ny), int(storage)
+        self.lattice = int(lattice)
+        self.npop = 32 if self.lattice == D2Q16_SPLIT_I else 50
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._opts = default_opts(**opts)
         self._bcs = make_bcs(bcs)
         h = ctypes.c_void_p()
-        st = lib().dvbm_create(ctypes.byref(h), D2Q25_SPLIT_II, self.Nx, self.Ny, float(Pr), float(gamma),
+        st = lib().dvbm_create(ctypes.byref(h), self.lattice, self.Nx, self.Ny, float(Pr), float(gamma),
                                float(mu), self._bcs, self.storage, ctypes.byref(self._opts),
                                ctypes.c_void_p(self.stream.cuda_stream))
         _check(st, None)
@@ -220,11 +222,11 @@ class Simulation:
         return self
 
     def populations(self, buf=None):
-        """View of a packed state as [50, Ny, Nx] (float64 or float32 deviations)."""
+        """View of a packed state as [npop, Ny, Nx] (float64 or float32 deviations)."""
         torch = _torch()
         buf = self.get_state() if buf is None else buf
         dt = torch.float64 if self.storage == FP64 else torch.float32
-        return buf[:-8].view(dt).view(50, self.Ny, self.Nx)
+        return buf[:-8].view(dt).view(self.npop, self.Ny, self.Nx)
 
     def record(self, every: int):
         """Keep checkpoints every `every` steps of the next init + step run."""
@@ -261,11 +263,15 @@ class Simulation:
         return int(lib().dvbm_steps_taken(self._h))
 
 
-def abi_velocities(R: float = 1.0, T_ref: float = 1.0):
-    """Discrete velocities (vx, vy) of the ABI population order c = 5 p + q
-    (node order 0, +a, -a, +b, -b; a = sqrt(5 - sqrt 10), b = sqrt(5 + sqrt 10))."""
-    a, b = np.sqrt(5 - np.sqrt(10)), np.sqrt(5 + np.sqrt(10))
-    xi = np.array([0.0, a, -a, b, -b]) * np.sqrt(R * T_ref)
-    vx = np.repeat(xi, 5)
-    vy = np.tile(xi, 5)
-    return vx, vy
+def abi_velocities(R: float = 1.0, T_ref: float = 1.0, lattice: int = D2Q25_SPLIT_II):
+    """Discrete velocities (vx, vy) of the ABI population order c = n p + q.
+    D2Q25: node order 0, +a, -a, +b, -b with a = sqrt(5 - sqrt 10), b = sqrt(5 + sqrt 10);
+    D2Q16: +a, -a, +b, -b with a = sqrt(3 - sqrt 6), b = sqrt(3 + sqrt 6)."""
+    if lattice == D2Q16_SPLIT_I:
+        a, b = np.sqrt(3 - np.sqrt(6)), np.sqrt(3 + np.sqrt(6))
+        xi = np.array([a, -a, b, -b]) * np.sqrt(R * T_ref)
+    else:
+        a, b = np.sqrt(5 - np.sqrt(10)), np.sqrt(5 + np.sqrt(10))
+        xi = np.array([0.0, a, -a, b, -b]) * np.sqrt(R * T_ref)
+    n = len(xi)
+    return np.repeat(xi, n), np.tile(xi, n)

@@ -8,11 +8,11 @@ from oracle import dvbm_oracle as O
 DT = torch.float64
 
 
-def oracle_run(F, Pr, gamma, mu, dt, nsteps, bcs=None, R=1.0, T_ref=1.0, beta=1.2):
+def oracle_run(F, Pr, gamma, mu, dt, nsteps, bcs=None, R=1.0, T_ref=1.0, beta=1.2, split="II"):
     t = lambda a: torch.tensor(np.asarray(a), dtype=DT)
     Ny, Nx = F.rho.shape
     grid = O.Grid(Nx, Ny, F.Lx, F.Ly, bcs) if bcs else O.Grid(Nx, Ny, F.Lx, F.Ly)
-    P = O.Params(Pr=Pr, gamma=gamma, mu=mu, R=R, T_ref=T_ref, beta=beta)
+    P = O.Params(Pr=Pr, gamma=gamma, mu=mu, R=R, T_ref=T_ref, beta=beta, split=split)
     s = O.Simulation(grid, P, t(F.rho), t(F.ux), t(F.uy), t(F.T), dt=dt)
     s.run(nsteps)
     rho, ux, uy, T = s.fields()
@@ -21,8 +21,8 @@ def oracle_run(F, Pr, gamma, mu, dt, nsteps, bcs=None, R=1.0, T_ref=1.0, beta=1.
 
 def abi_to_oracle_perm(lat):
     """perm[i] = ABI population index of the oracle's population i (matched by velocity)."""
-    from paper_2510_04197_gb300.dvbm import abi_velocities
-    vx, vy = abi_velocities(lat.R, lat.T_ref)
+    from paper_2510_04197_gb300.dvbm import abi_velocities, D2Q16_SPLIT_I, D2Q25_SPLIT_II
+    vx, vy = abi_velocities(lat.R, lat.T_ref, D2Q16_SPLIT_I if lat.Q == 16 else D2Q25_SPLIT_II)
     perm = []
     for i in range(lat.Q):
         d = np.abs(vx - float(lat.vx[i])) + np.abs(vy - float(lat.vy[i]))

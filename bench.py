@@ -62,12 +62,12 @@ def workload_config(N):
 STEP_KERNEL_SOURCES = ("dvbm_device.cuh", "dvbm_step.cu")
 
 
-def kernel_source_hash():
-    """Hash of the sources the step kernel is compiled from (the committed
-    ncu figures are only used while this hash matches)."""
+def kernel_source_hash(sources=STEP_KERNEL_SOURCES):
+    """Hash of the sources a step kernel is compiled from (the committed ncu
+    figures are only used while this hash matches)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2510_04197_gb300", "csrc")
-    for fn in STEP_KERNEL_SOURCES:
+    for fn in sources:
         h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:16]
 
@@ -87,7 +87,7 @@ def profile_traffic(kernel_key):
         with open(PROFILE_TRAFFIC) as fh:
             t = json.load(fh)
         e = t.get(kernel_key)
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash(tuple(e.get("sources", STEP_KERNEL_SOURCES))):
             return e
     except Exception:
         pass
@@ -360,6 +360,8 @@ def main():
                            "dtype": "f32 storage / f64 moments+equilibria",
                            "roofline_hbm": {"bound": "hbm", "achieved": g32, "peak": hbm_peak, "unit": "GB/s",
                                             "frac": g32 / hbm_peak}}
+        t32 = profile_traffic("k_step_fp32dev")
+        line["fp32dev"]["roofline_hbm"]["traffic"] = t32["dram_bytes_per_cell"] * N * N if t32 else None
     if "d2q16" in results:
         r16 = results["d2q16"]
         g16 = BYTES_PER_CELL["d2q16"] * N * N / (r16["kernel_ms"] * 1e-3) / 1e9
@@ -367,6 +369,8 @@ def main():
                                  "dtype": "f64", "workload": "same flow, total-energy split (I) on D2Q16",
                                  "roofline_hbm": {"bound": "hbm", "achieved": g16, "peak": hbm_peak, "unit": "GB/s",
                                                   "frac": g16 / hbm_peak}}
+        t16 = profile_traffic("k_step16")
+        line["d2q16_split_I"]["roofline_hbm"]["traffic"] = t16["dram_bytes_per_cell"] * N * N if t16 else None
     line["e2e"] = e2e
     if not args.no_adjoint:
         line["adjoint"] = adjoint_ratio(dvbm, inputs, torch)

@@ -37,10 +37,10 @@ differentiable torch ops, ``torch.autograd`` applied to it gives the exact
 gradient of the discrete map (the discrete adjoint), which the tests use as
 the adjoint oracle.
 
-Readings of the paper where it is silent or garbled are listed in the design doc
-(the D2Q25 weights carry a /60; the third-order QE moment is the symmetric
-tensor whose contraction equals the heat-flux constraint; b = 0 gives a zero
-limited slope; the time step is fixed from the initial field).
+Where the paper is silent or garbled this module takes these readings: the
+D2Q25 weights carry a /60; the third-order QE moment is the symmetric tensor
+whose contraction equals the heat-flux constraint; b = 0 gives a zero limited
+slope; the time step is fixed from the initial field.
 """
 from __future__ import annotations
 

@@ -200,6 +200,13 @@ __device__ __forceinline__ void write_expansion(double* d, long long PL, const C
 
 }  // namespace q16
 
+// W_k He_n(xi_k)/n! of the four D2Q16 x-nodes as a constant-bank table (the
+// same constexpr values the unrolled helpers fold in), for the node loop.
+__constant__ double c_khq[4][4] = {{q16::khq(0, 0), q16::khq(0, 1), q16::khq(0, 2), q16::khq(0, 3)},
+                                   {q16::khq(1, 0), q16::khq(1, 1), q16::khq(1, 2), q16::khq(1, 3)},
+                                   {q16::khq(2, 0), q16::khq(2, 1), q16::khq(2, 2), q16::khq(2, 3)},
+                                   {q16::khq(3, 0), q16::khq(3, 1), q16::khq(3, 2), q16::khq(3, 3)}};
+
 template <int PRC, bool RAT>
 __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, double* __restrict__ dst, Geom G,
                                                 Phys P, unsigned int* __restrict__ flag) {
@@ -214,31 +221,49 @@ __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, 
   const Mom m = cell_moments(s, PL);
   const Co C = coeffs<PRC>(m, P);
   if (C.bad) atomicOr(flag, 1u);
-#define Q16_NODE(p)                                                                              \
-  {                                                                                              \
-    double h[4], tf[4], hh[4], tg[4];                                                            \
-    hf<p>(C, h); expand(h, tf); hg<p>(C, hh); expand(hh, tg);                                    \
-    _Pragma("unroll") for (int q = 0; q < 4; ++q) {                                              \
-      _Pragma("unroll") for (int k = 0; k < 2; ++k) {                                            \
-        const int c = 4 * p + q + 16 * k;                                                        \
-        const double* pc = s + c * PL;                                                           \
-        double fx, fy;                                                                           \
-        if constexpr (RAT) {                                                                     \
-          fx = flux_difference_rat(pc, 1, P.lp, P.lq, sgn(p));                                   \
-          fy = flux_difference_rat(pc, PT, P.lp, P.lq, sgn(q));                                  \
-        } else {                                                                                 \
-          fx = flux_difference_int(pc, 1, P.hq, sgn(p));                                         \
-          fy = flux_difference_int(pc, PT, P.hq, sgn(q));                                        \
-        }                                                                                        \
-        double v = fma(C.a1, __ldg(pc), k == 0 ? tf[q] : tg[q]);                                 \
-        v = fma(RAT ? -P.kxr[p] : -P.kxv[p], fx, v);                                             \
-        v = fma(RAT ? -P.kyr[q] : -P.kyv[q], fy, v);                                             \
-        d[c * PL] = v;                                                                           \
-      }                                                                                          \
-    }                                                                                            \
+  // x-nodes p = 0..3 in a run-time loop (one copy of the body: the kernel
+  // stays small enough for the instruction cache); the y-nodes are unrolled.
+#pragma unroll 1
+  for (int p = 0; p < 4; ++p) {
+    const double k0 = c_khq[p][0], k1 = c_khq[p][1], k2 = c_khq[p][2], k3 = c_khq[p][3];
+    double h[4], tf[4], hh[4], tg[4];
+    // same operation order as hf<p> / hg<p>
+    h[0] = fma(k3, C.f30, fma(k2, C.f20, fma(k1, C.f10, k0 * C.f00)));
+    h[1] = fma(k2, C.f21, fma(k1, C.f11, k0 * C.f01));
+    h[2] = fma(k1, C.f12, k0 * C.f02);
+    h[3] = k0 * C.f03;
+    hh[0] = fma(k2, C.g20, fma(k1, C.g10, k0 * C.g00));
+    hh[1] = fma(k1, C.g11, k0 * C.g01);
+    hh[2] = k0 * C.g02;
+    hh[3] = 0.0;
+    expand(h, tf);
+    expand(hh, tg);
+    const int sx = (p & 1) ? -1 : 1;  // nodes +a, -a, +b, -b
+    // kx of node p: kxv[1] = -kxv[0] and kxv[3] = -kxv[2] exactly
+    const double kb = p < 2 ? (RAT ? P.kxr[0] : P.kxv[0]) : (RAT ? P.kxr[2] : P.kxv[2]);
+    const double kx = kb * (double)sx;
+    const long long pbase = (long long)(4 * p) * PL;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const long long co = pbase + (long long)(q + 16 * k) * PL;
+        const double* pc = s + co;
+        double fx, fy;
+        if constexpr (RAT) {
+          fx = flux_difference_rat(pc, 1, P.lp, P.lq, sx);
+          fy = flux_difference_rat(pc, PT, P.lp, P.lq, sgn(q));
+        } else {
+          fx = flux_difference_int(pc, 1, P.hq, sx);
+          fy = flux_difference_int(pc, PT, P.hq, sgn(q));
+        }
+        double v = fma(C.a1, __ldg(pc), k == 0 ? tf[q] : tg[q]);
+        v = fma(-kx, fx, v);
+        v = fma(RAT ? -P.kyr[q] : -P.kyv[q], fy, v);
+        d[co] = v;
+      }
+    }
   }
-  Q16_NODE(0) Q16_NODE(1) Q16_NODE(2) Q16_NODE(3)
-#undef Q16_NODE
 }
 
 __global__ void k_init16(double* __restrict__ dst, const double* __restrict__ rho, const double* __restrict__ ux,

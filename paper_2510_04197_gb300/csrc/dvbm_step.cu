@@ -37,6 +37,94 @@ __device__ __forceinline__ void load_node(const S* __restrict__ src, long long p
   }
 }
 
+// W_k He_n(xi_k)/n! of the five x-nodes as a constant-bank table, for the
+// node loop below (the same constexpr values the unrolled code folds in).
+__constant__ double c_kh[5][5] = {
+    {kh(0, 0), kh(0, 1), kh(0, 2), kh(0, 3), kh(0, 4)}, {kh(1, 0), kh(1, 1), kh(1, 2), kh(1, 3), kh(1, 4)},
+    {kh(2, 0), kh(2, 1), kh(2, 2), kh(2, 3), kh(2, 4)}, {kh(3, 0), kh(3, 1), kh(3, 2), kh(3, 3), kh(3, 4)},
+    {kh(4, 0), kh(4, 1), kh(4, 2), kh(4, 3), kh(4, 4)}};
+
+// h^b_p of the f and g expansions for a non-central x-node p chosen at run
+// time (same operation order as hf_of<p> / hg_of<p>, p != 0).
+__device__ __forceinline__ void hfg_node(int p, const Coeffs& C, double (&hf)[5], double (&hg)[3]) {
+  const double k0 = c_kh[p][0], k1 = c_kh[p][1], k2 = c_kh[p][2], k3 = c_kh[p][3], k4 = c_kh[p][4];
+  hf[0] = fma(k4, C.f40, fma(k3, C.f30, fma(k2, C.f20, fma(k1, C.f10, k0 * C.f00))));
+  hf[1] = fma(k3, C.f31, fma(k2, C.f21, fma(k1, C.f11, k0 * C.f01)));
+  hf[2] = fma(k2, C.f22, fma(k1, C.f12, k0 * C.f02));
+  hf[3] = fma(k1, C.f13, k0 * C.f03);
+  hf[4] = k0 * C.f04;
+  hg[0] = fma(k2, C.g20, fma(k1, C.g10, k0 * C.g00));
+  hg[1] = fma(k1, C.g11, k0 * C.g01);
+  hg[2] = k0 * C.g02;
+}
+
+// The ten populations (f and g, y-nodes q = 0..4) of x-node p: collision
+// target from the sum-factorised expansion, upwind-limited flux differences
+// along x (p != 0) and y (q != 0), new value.  CENTER: p = 0 (xi_x = 0, no
+// x-flux); otherwise p = 1..4 at run time, so one copy of this body serves
+// the four moving x-nodes and the kernel's code stays small enough for the
+// instruction cache.
+template <class S, bool RAT, bool CENTER>
+__device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* __restrict__ d, long long PL,
+                                            long long PT, const Coeffs& C, const Phys& P, float a1f) {
+  typedef typename StoreT<S>::adv_t A;
+  double hf[5], tf[5], hg[3], tg[5];
+  if constexpr (CENTER) {
+    hf_of<0>(C, hf);
+    hg_of<0>(C, hg);
+  } else {
+    hfg_node(p, C, hf, hg);
+  }
+  expand_q5(hf, tf);
+  expand_q3(hg, tg);
+  // x-node sign and flux factor (p = 1, 3: +xi; p = 2, 4: -xi); warp-uniform selects
+  const int sx = (p & 1) ? 1 : -1;
+  const int pa = (p + 1) >> 1;  // 1 for p = 1, 2; 2 for p = 3, 4
+  double kx = 0.0;
+  float kxf = 0.f;
+  if constexpr (!CENTER) {
+    if constexpr (sizeof(S) == 8) {
+      const double k_a = RAT ? P.kxr[1] : P.kxv[1], k_b = RAT ? P.kxr[3] : P.kxv[3];
+      kx = (pa == 1 ? k_a : k_b) * (double)sx;  // kxv[2] = -kxv[1], kxv[4] = -kxv[3] exactly
+    } else {
+      kxf = (pa == 1 ? P.kxvf[1] : P.kxvf[3]) * (float)sx;
+    }
+  }
+  const A hb = (A)P.hb;
+  const long long pbase = (long long)(5 * p) * PL;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const long long co = pbase + (long long)(q + 25 * k) * PL;
+      const S* pc = s + co;
+      const double t = k == 0 ? tf[q] : tg[q];
+      A fx = 0, fy = 0;
+      if constexpr (sizeof(S) == 8) {
+        if constexpr (RAT) {
+          if (!CENTER) fx = flux_difference_rat((const double*)pc, 1, P.lp, P.lq, sx);
+          if (sgn_of(q) != 0) fy = flux_difference_rat((const double*)pc, PT, P.lp, P.lq, sgn_of(q));
+        } else {
+          if (!CENTER) fx = flux_difference_int((const double*)pc, 1, P.hq, sx);
+          if (sgn_of(q) != 0) fy = flux_difference_int((const double*)pc, PT, P.hq, sgn_of(q));
+        }
+        double v = fma(C.a1, (double)__ldg(pc), t);
+        if (!CENTER) v = fma(-kx, (double)fx, v);
+        if (sgn_of(q) != 0) v = fma(RAT ? -P.kyr[q] : -P.kyv[q], (double)fy, v);
+        d[co] = (S)v;
+      } else {
+        if (!CENTER) fx = sx > 0 ? flux_difference<1, S>(pc, 1, (S)hb) : flux_difference<-1, S>(pc, 1, (S)hb);
+        if (sgn_of(q) > 0) fy = flux_difference<1, S>(pc, PT, (S)hb);
+        if (sgn_of(q) < 0) fy = flux_difference<-1, S>(pc, PT, (S)hb);
+        float adv = 0.f;
+        if (!CENTER) adv = kxf * (float)fx;
+        if (sgn_of(q) != 0) adv = fmaf(P.kyvf[q], (float)fy, adv);
+        d[co] = (S)(fmaf(a1f, (float)__ldg(pc), __double2float_rn(t)) - adv);
+      }
+    }
+  }
+}
+
 template <class S, int PRC, bool RAT>
 __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
                                               unsigned int* __restrict__ flag) {
@@ -73,61 +161,14 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
     C.f00 -= C.k1 * P.fref0;
     C.g00 -= C.k1 * P.gref0;
   }
-
-  typedef typename StoreT<S>::adv_t A;
-  const A hb = (A)P.hb;
   // FP32DEV: new deviation = a1 * dev + (t - k1 * ref) - advection, with the
   // bracket (equilibrium evaluation minus the relaxed reference) in double
   const float a1f = (float)C.a1;
-  constexpr bool rational = RAT;
 
   // ---- phase B: populations, x-node by x-node ----
-#define DVBM_NODE(p)                                                                       \
-  {                                                                                         \
-    double hf[5], tf[5], hg[3], tg[5];                                                      \
-    hf_of<p>(C, hf); expand_q5(hf, tf);                                                     \
-    hg_of<p>(C, hg); expand_q3(hg, tg);                                                     \
-    _Pragma("unroll") for (int q = 0; q < 5; ++q) {                                         \
-      _Pragma("unroll") for (int k = 0; k < 2; ++k) {                                       \
-        const int c = 5 * p + q + 25 * k;                                                   \
-        const S* pc = s + c * PL;                                                           \
-        const double t = k == 0 ? tf[q] : tg[q];                                            \
-        A fx = 0, fy = 0;                                                                   \
-        if constexpr (sizeof(S) == 8) {                                                     \
-          if constexpr (rational) {                                                         \
-            if (sgn_of(p) != 0) fx = flux_difference_rat((const double*)pc, 1, P.lp, P.lq, sgn_of(p));   \
-            if (sgn_of(q) != 0) fy = flux_difference_rat((const double*)pc, PT, P.lp, P.lq, sgn_of(q));  \
-          } else {                                                                          \
-            if (sgn_of(p) != 0) fx = flux_difference_int((const double*)pc, 1, P.hq, sgn_of(p)); \
-            if (sgn_of(q) != 0) fy = flux_difference_int((const double*)pc, PT, P.hq, sgn_of(q)); \
-          }                                                                                 \
-        } else {                                                                            \
-          if (sgn_of(p) > 0) fx = flux_difference<1, S>(pc, 1, (S)hb);                      \
-          if (sgn_of(p) < 0) fx = flux_difference<-1, S>(pc, 1, (S)hb);                     \
-          if (sgn_of(q) > 0) fy = flux_difference<1, S>(pc, PT, (S)hb);                     \
-          if (sgn_of(q) < 0) fy = flux_difference<-1, S>(pc, PT, (S)hb);                    \
-        }                                                                                   \
-        if constexpr (sizeof(S) == 8) {                                                     \
-          double v = fma(C.a1, (double)__ldg(pc), t);                                       \
-          if (sgn_of(p) != 0) v = fma(rational ? -P.kxr[p] : -P.kxv[p], (double)fx, v);    \
-          if (sgn_of(q) != 0) v = fma(rational ? -P.kyr[q] : -P.kyv[q], (double)fy, v);    \
-          d[c * PL] = (S)v;                                                                 \
-        } else {                                                                            \
-          const double base = t;                                                            \
-          float adv = 0.f;                                                                  \
-          if (sgn_of(p) != 0) adv = P.kxvf[p] * (float)fx;                                  \
-          if (sgn_of(q) != 0) adv = fmaf(P.kyvf[q], (float)fy, adv);                        \
-          d[c * PL] = (S)(fmaf(a1f, (float)__ldg(pc), __double2float_rn(base)) - adv);     \
-        }                                                                                   \
-      }                                                                                     \
-    }                                                                                       \
-  }
-  DVBM_NODE(0)
-  DVBM_NODE(1)
-  DVBM_NODE(2)
-  DVBM_NODE(3)
-  DVBM_NODE(4)
-#undef DVBM_NODE
+  node_update<S, RAT, true>(0, s, d, PL, PT, C, P, a1f);
+#pragma unroll 1
+  for (int p = 1; p < 5; ++p) node_update<S, RAT, false>(p, s, d, PL, PT, C, P, a1f);
 }
 
 template <class S>

@@ -409,27 +409,15 @@ __device__ __forceinline__ int slope_branch_rat(long long Da, long long Db, long
   return y >= rb ? 2 : 3;
 }
 
-__device__ __forceinline__ double advection_adjoint_rat(const double* __restrict__ X, const double* __restrict__ L,
-                                                        long long stride, int lp, int lq, int sgn) {
-  double xv[5], lv[5];
+// lambda part of the rational-beta advection adjoint, given the minmod branch
+// codes bm, b0, bp of the slopes sigma_{c-1}, sigma_c, sigma_{c+1} along the
+// stride.  Returns 4 lq sum_{c'} lambda(c') dF(c')/dX(c).
+__device__ __forceinline__ double adjoint_combine_rat(const double* __restrict__ L, long long stride, int bm, int b0,
+                                                      int bp, int lp, int lq, int sgn) {
+  double lv[5];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    xv[k] = __ldg(X + (k - 2) * stride);
-    lv[k] = __ldg(L + (k - 2) * stride);
-  }
-  const int EX = max(max(max(bexp(xv[0]), bexp(xv[1])), max(bexp(xv[2]), bexp(xv[3]))), bexp(xv[4]));
+  for (int k = 0; k < 5; ++k) lv[k] = __ldg(L + (k - 2) * stride);
   const long long lp2 = 2 * lp, q = lq, q4 = 4 * lq;
-  long long D[4];
-  {
-    long long xi[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) xi[k] = to_block_fixed52(xv[k], EX);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) D[k] = xi[k + 1] - xi[k];
-  }
-  const int bm = slope_branch_rat(D[0], D[1], lp2, q);
-  const int b0 = slope_branch_rat(D[1], D[2], lp2, q);
-  const int bp = slope_branch_rat(D[2], D[3], lp2, q);
   const int EL = max(max(max(bexp(lv[0]), bexp(lv[1])), max(bexp(lv[2]), bexp(lv[3]))), bexp(lv[4]));
   long long l[5];
 #pragma unroll
@@ -446,6 +434,27 @@ __device__ __forceinline__ double advection_adjoint_rat(const double* __restrict
   }
   if (EL < 64) return 0.0;
   return ll_to_double_scaled(Xb, EL - 1072);  // lambda was scaled by 2^(1072 - EL)
+}
+
+__device__ __forceinline__ double advection_adjoint_rat(const double* __restrict__ X, const double* __restrict__ L,
+                                                        long long stride, int lp, int lq, int sgn) {
+  double xv[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) xv[k] = __ldg(X + (k - 2) * stride);
+  const int EX = max(max(max(bexp(xv[0]), bexp(xv[1])), max(bexp(xv[2]), bexp(xv[3]))), bexp(xv[4]));
+  const long long lp2 = 2 * lp, q = lq;
+  long long D[4];
+  {
+    long long xi[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) xi[k] = to_block_fixed52(xv[k], EX);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D[k] = xi[k + 1] - xi[k];
+  }
+  const int bm = slope_branch_rat(D[0], D[1], lp2, q);
+  const int b0 = slope_branch_rat(D[1], D[2], lp2, q);
+  const int bp = slope_branch_rat(D[2], D[3], lp2, q);
+  return adjoint_combine_rat(L, stride, bm, b0, bp, lp, lq, sgn);
 }
 
 // ------------------------------------------------------------------- kernels
@@ -516,10 +525,13 @@ __global__ void __launch_bounds__(256) k_adjoint_local(const double* __restrict_
 }
 
 // k_adjoint_adv: Lout += -(dt/dx) v_x sum_c' Lin(c') dF_x(c')/dX(c) - (same in y),
-// one thread per (cell, population); blockIdx.z = population.
-template <bool RAT>
+// one thread per (cell, population); blockIdx.z = population.  CODED: the
+// minmod branches come from the codes the recomputed forward step recorded
+// (periodic neighbours wrap), so X is not read at all.
+template <bool RAT, bool CODED>
 __global__ void __launch_bounds__(256) k_adjoint_adv(const double* __restrict__ X, const double* __restrict__ Lin,
-                                                     double* __restrict__ Lout, Geom G, Phys P) {
+                                                     double* __restrict__ Lout,
+                                                     const unsigned char* __restrict__ codes, Geom G, Phys P) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   const int c = blockIdx.z;
@@ -531,7 +543,21 @@ __global__ void __launch_bounds__(256) k_adjoint_adv(const double* __restrict__ 
   const double* xc = X + off;
   const double* lc = Lin + off;
   double v = Lout[off];
-  if (RAT) {
+  if constexpr (CODED) {
+    const unsigned char* cp = codes + (long long)c * G.Nx * G.Ny;
+    const long long row = (long long)y * G.Nx;
+    if (sx != 0) {
+      const int xm = x == 0 ? G.Nx - 1 : x - 1, xp = x == G.Nx - 1 ? 0 : x + 1;
+      const int bm = __ldg(cp + row + xm) & 3, b0 = __ldg(cp + row + x) & 3, bp = __ldg(cp + row + xp) & 3;
+      v = fma(-P.kxr[pn], adjoint_combine_rat(lc, 1, bm, b0, bp, P.lp, P.lq, sx), v);
+    }
+    if (sy != 0) {
+      const int ym = y == 0 ? G.Ny - 1 : y - 1, yp = y == G.Ny - 1 ? 0 : y + 1;
+      const int bm = (__ldg(cp + (long long)ym * G.Nx + x) >> 2) & 3, b0 = (__ldg(cp + row + x) >> 2) & 3,
+                bp = (__ldg(cp + (long long)yp * G.Nx + x) >> 2) & 3;
+      v = fma(-P.kyr[qn], adjoint_combine_rat(lc, G.pitch, bm, b0, bp, P.lp, P.lq, sy), v);
+    }
+  } else if constexpr (RAT) {
     if (sx != 0) v = fma(-P.kxr[pn], advection_adjoint_rat(xc, lc, 1, P.lp, P.lq, sx), v);
     if (sy != 0) v = fma(-P.kyr[qn], advection_adjoint_rat(xc, lc, G.pitch, P.lp, P.lq, sy), v);
   } else {
@@ -625,8 +651,8 @@ __global__ void __launch_bounds__(256) k_adjoint_init(const double* __restrict__
 // ------------------------------------------------------------------ wrappers
 int adjoint_blocks(const Geom& G) { return ((G.Nx + 31) / 32) * ((G.Ny + 7) / 8); }
 
-cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial, const Geom& G,
-                                const Phys& P, cudaStream_t st) {
+cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial,
+                                const unsigned char* codes, const Geom& G, const Phys& P, cudaStream_t st) {
   dim3 block(32, 8), grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
   if (P.prc < 0) k_adjoint_local<-1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
   else if (P.prc > 0) k_adjoint_local<1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
@@ -634,8 +660,9 @@ cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid3(grid.x, grid.y, NPOP);
-  if (P.lq > 0) k_adjoint_adv<true><<<grid3, block, 0, st>>>(X, Lin, Lout, G, P);
-  else k_adjoint_adv<false><<<grid3, block, 0, st>>>(X, Lin, Lout, G, P);
+  if (P.lq > 0 && codes) k_adjoint_adv<true, true><<<grid3, block, 0, st>>>(X, Lin, Lout, codes, G, P);
+  else if (P.lq > 0) k_adjoint_adv<true, false><<<grid3, block, 0, st>>>(X, Lin, Lout, nullptr, G, P);
+  else k_adjoint_adv<false, false><<<grid3, block, 0, st>>>(X, Lin, Lout, nullptr, G, P);
   return cudaGetLastError();
 }
 

@@ -503,19 +503,30 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
   const int k = c->record_every;
   const int nblk = adjoint_blocks(c->G);
   const size_t ncell = (size_t)c->Nx * c->Ny;
-  // work buffers: two adjoint states, k segment states, partial sums
+  // work buffers: two adjoint states, k segment states (k + 1 when the
+  // recompute records minmod branch codes: the segment's last state is stepped
+  // too), the codes of k steps (NPOP bytes per cell and step), partial sums
   void* lam[2] = {nullptr, nullptr};
   std::vector<void*> seg;
   double* part = nullptr;
+  unsigned char* codes = nullptr;
   const long long nslots = (n + 2) * (long long)nblk * 4;
+  const size_t code_step = (size_t)NPOP * ncell;
+  bool coded = c->P.lq > 0;
+  if (coded && cudaMalloc(&codes, (size_t)k * code_step) != cudaSuccess) {
+    cudaGetLastError();  // not enough memory for the codes: derive the branches from the states instead
+    codes = nullptr;
+    coded = false;
+  }
   dvbm_status s = DVBM_OK;
   auto cleanup = [&]() {
     for (int i = 0; i < 2; ++i) if (lam[i]) c->pool.push_back(lam[i]);
     for (void* p : seg) c->pool.push_back(p);
     if (part) cudaFree(part);
+    if (codes) cudaFree(codes);
   };
   for (int i = 0; i < 2 && s == DVBM_OK; ++i) s = take_buffer(c, &lam[i]);
-  for (int i = 0; i < k && s == DVBM_OK; ++i) {
+  for (int i = 0; i < k + (coded ? 1 : 0) && s == DVBM_OK; ++i) {
     void* b = nullptr;
     s = take_buffer(c, &b);
     if (s == DVBM_OK) seg.push_back(b);
@@ -541,13 +552,16 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
   for (long long j = nseg - 1; j >= 0 && e == cudaSuccess; --j) {
     const long long S = j * k, E = std::min<long long>((j + 1) * k, n);
     e = cudaMemcpyAsync(seg[0], c->ckpt[j], c->state_bytes_dev, cudaMemcpyDeviceToDevice, c->stream);
-    for (long long t = 0; t + 1 < E - S && e == cudaSuccess; ++t) {
-      e = launch_step(0, seg[t], seg[t + 1], c->G, c->P, c->flag, c->stream);
-      if (e == cudaSuccess) e = launch_ghost(0, seg[t + 1], c->G, c->P, c->M, c->bc, c->stream);
+    const long long nrec = coded ? E - S : E - S - 1;
+    for (long long t = 0; t < nrec && e == cudaSuccess; ++t) {
+      if (coded) e = launch_step_codes(seg[t], seg[t + 1], c->G, c->P, c->flag, codes + t * code_step, c->stream);
+      else e = launch_step(0, seg[t], seg[t + 1], c->G, c->P, c->flag, c->stream);
+      if (e == cudaSuccess && t + 1 < E - S) e = launch_ghost(0, seg[t + 1], c->G, c->P, c->M, c->bc, c->stream);
     }
     for (long long t = E - S - 1; t >= 0 && e == cudaSuccess; --t) {
       e = launch_adjoint_step((const double*)seg[t], (const double*)lam[a], (double*)lam[1 - a],
-                              part + slot * nblk * 4, c->G, c->P, c->stream);
+                              part + slot * nblk * 4, coded ? codes + t * code_step : nullptr, c->G, c->P,
+                              c->stream);
       ++slot;
       a = 1 - a;
       if (e == cudaSuccess) e = launch_ghost(0, lam[a], c->G, c->P, c->M, per, c->stream);

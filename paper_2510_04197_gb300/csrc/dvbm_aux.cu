@@ -54,11 +54,16 @@ __global__ void k_init(S* __restrict__ dst, const double* __restrict__ rho, cons
   write_expansion<S>(dst + cell_index(G, y, x), G.plane, C, P, nullptr, nullptr);
 }
 
-// one thread per (side, layer k, position along the side); sides 0..3 = xlo, xhi, ylo, yhi
+// one thread per (side, layer k, position along the side, population);
+// sides 0..3 = xlo, xhi, ylo, yhi, blockIdx.z = population.  Periodic and
+// zero-gradient sides copy one population per thread; a wall side needs all
+// populations of its mirror cell and is done by the blockIdx.z = 0 slice.
 template <class S>
 __global__ void k_ghost(S* __restrict__ buf, Geom G, Phys P, Macro M, BCDev bc) {
   const int side = blockIdx.y;
   const int kind = bc.kind[side];
+  const int pop = blockIdx.z;
+  if (kind == 2 && pop != 0) return;
   const int len = side < 2 ? G.Ny : G.Nx;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * len) return;
@@ -78,8 +83,7 @@ __global__ void k_ghost(S* __restrict__ buf, Geom G, Phys P, Macro M, BCDev bc) 
   S* gptr = buf + cell_index(G, gy, gx);
   const S* bptr = buf + cell_index(G, by, bx);
   if (kind != 2) {
-#pragma unroll 10
-    for (int c = 0; c < NPOP; ++c) gptr[c * PL] = bptr[c * PL];
+    gptr[pop * PL] = bptr[pop * PL];
     return;
   }
   // wall: equilibrium at the ghost state + non-equilibrium part of the mirror cell
@@ -210,7 +214,7 @@ cudaError_t launch_init(int storage, void* dst, const double* rho, const double*
 cudaError_t launch_ghost(int storage, void* buf, const Geom& G, const Phys& P, const Macro& M, const BCDev& bc,
                          cudaStream_t st) {
   const int len = G.Nx > G.Ny ? G.Nx : G.Ny;
-  dim3 b(128), g((2 * len + 127) / 128, 4);
+  dim3 b(128), g((2 * len + 127) / 128, 4, NPOP);
   if (storage == 0) k_ghost<double><<<g, b, 0, st>>>((double*)buf, G, P, M, bc);
   else k_ghost<float><<<g, b, 0, st>>>((float*)buf, G, P, M, bc);
   return cudaGetLastError();

@@ -322,9 +322,13 @@ __global__ void __launch_bounds__(256) k_totals16(const double* __restrict__ src
 }
 
 // ghost layers: periodic / zero-gradient copies or the wall closure (Sec. III.E)
+// same thread layout as k_ghost: blockIdx.z = population for copied sides,
+// the z = 0 slice for wall sides
 __global__ void k_ghost16(double* __restrict__ buf, Geom G, Phys P, Macro M, BCDev bc) {
   const int side = blockIdx.y;
   const int kind = bc.kind[side];
+  const int pop = blockIdx.z;
+  if (kind == 2 && pop != 0) return;
   const int len = side < 2 ? G.Ny : G.Nx;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * len) return;
@@ -344,7 +348,7 @@ __global__ void k_ghost16(double* __restrict__ buf, Geom G, Phys P, Macro M, BCD
   double* gptr = buf + cell_index(G, gy, gx);
   const double* bptr = buf + cell_index(G, by, bx);
   if (kind != 2) {
-    for (int c = 0; c < q16::NP; ++c) gptr[c * PL] = bptr[c * PL];
+    gptr[pop * PL] = bptr[pop * PL];
     return;
   }
   const q16::Mom m = q16::cell_moments(bptr, PL);
@@ -411,7 +415,7 @@ cudaError_t launch_totals16(const void* src, double* partial, int nblocks, const
 cudaError_t launch_ghost16(void* buf, const Geom& G, const Phys& P, const Macro& M, const BCDev& bc,
                            cudaStream_t st) {
   const int len = G.Nx > G.Ny ? G.Nx : G.Ny;
-  dim3 b(128), g((2 * len + 127) / 128, 4);
+  dim3 b(128), g((2 * len + 127) / 128, 4, q16::NP);
   k_ghost16<<<g, b, 0, st>>>((double*)buf, G, P, M, bc);
   return cudaGetLastError();
 }

@@ -454,6 +454,43 @@ __device__ __forceinline__ double flux_difference_rat(const double* __restrict__
   return ll_to_double_scaled(F, E - 1074);  // value = F 2^(E - 1074)
 }
 
+// slope_rat together with the minmod branch it took: 0 (a and b differ in
+// sign), 1 (2 lp Da), 2 (lq (Da + Db)), 3 (2 lp Db), ties resolved in that
+// order.  The value equals slope_rat's.
+__device__ __forceinline__ long long slope_rat_code(long long Da, long long Db, long long lp2, long long lq,
+                                                    int& code) {
+  const long long ra = lp2 * Da, rb = lp2 * Db, y = lq * (Da + Db);
+  int br;
+  if (Da >= 0) br = (ra <= y && ra <= rb) ? 1 : (y <= rb ? 2 : 3);
+  else br = (ra >= y && ra >= rb) ? 1 : (y >= rb ? 2 : 3);
+  if ((Da ^ Db) < 0) br = 0;
+  code = br;
+  return br == 0 ? 0ll : (br == 1 ? ra : (br == 2 ? y : rb));
+}
+
+// flux_difference_rat that also returns the branch code of the cell's own
+// slope sigma_j (first argument its backward, second its forward difference):
+// s_bc for v > 0, s_ab for v < 0.  The adjoint reads these codes instead of
+// re-deriving them from the state.
+__device__ __forceinline__ double flux_difference_rat_code(const double* __restrict__ ptr, long long stride, int lp,
+                                                           int lq, int sgn, int& code) {
+  const long long o0 = sgn > 0 ? -2 * stride : -stride;
+  const double a0 = __ldg(ptr + o0), a1 = __ldg(ptr + o0 + stride), a2 = __ldg(ptr + o0 + 2 * stride),
+               a3 = __ldg(ptr + o0 + 3 * stride);
+  const int E = max(max(bexp(a0), bexp(a1)), max(bexp(a2), bexp(a3)));
+  const long long x0 = to_block_fixed52(a0, E), x1 = to_block_fixed52(a1, E), x2 = to_block_fixed52(a2, E),
+                  x3 = to_block_fixed52(a3, E);
+  const long long Da = x1 - x0, Db = x2 - x1, Dc = x3 - x2;
+  const long long lp2 = 2 * lp, q4 = 4 * lq;
+  int c_ab, c_bc;
+  const long long s_ab = slope_rat_code(Da, Db, lp2, lq, c_ab);
+  const long long s_bc = slope_rat_code(Db, Dc, lp2, lq, c_bc);
+  code = sgn > 0 ? c_bc : c_ab;
+  const long long F = sgn > 0 ? q4 * Db + s_bc - s_ab : q4 * Db - s_bc + s_ab;
+  if (E < 64) return 0.0;
+  return ll_to_double_scaled(F, E - 1074);
+}
+
 template <int SGN, class T>
 __device__ __forceinline__ T flux_difference(const T* __restrict__ ptr, long long stride, T hb) {
   if constexpr (sizeof(T) == 8) {

@@ -64,9 +64,13 @@ __device__ __forceinline__ void hfg_node(int p, const Coeffs& C, double (&hf)[5]
 // x-flux); otherwise p = 1..4 at run time, so one copy of this body serves
 // the four moving x-nodes and the kernel's code stays small enough for the
 // instruction cache.
-template <class S, bool RAT, bool CENTER>
+// CODES (FP64, rational limiter only): also store, per population, the
+// minmod branch codes of the cell's own x and y slopes as one byte
+// (x | y << 2) at cd[pop * cplane]; the adjoint of the step reads them.
+template <class S, bool RAT, bool CENTER, bool CODES = false>
 __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* __restrict__ d, long long PL,
-                                            long long PT, const Coeffs& C, const Phys& P, float a1f) {
+                                            long long PT, const Coeffs& C, const Phys& P, float a1f,
+                                            unsigned char* __restrict__ cd = nullptr, long long cplane = 0) {
   typedef typename StoreT<S>::adv_t A;
   double hf[5], tf[5], hg[3], tg[5];
   if constexpr (CENTER) {
@@ -101,7 +105,12 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
       const double t = k == 0 ? tf[q] : tg[q];
       A fx = 0, fy = 0;
       if constexpr (sizeof(S) == 8) {
-        if constexpr (RAT) {
+        if constexpr (CODES) {
+          int cx = 0, cy = 0;
+          if (!CENTER) fx = flux_difference_rat_code((const double*)pc, 1, P.lp, P.lq, sx, cx);
+          if (sgn_of(q) != 0) fy = flux_difference_rat_code((const double*)pc, PT, P.lp, P.lq, sgn_of(q), cy);
+          cd[(long long)(5 * p + q + 25 * k) * cplane] = (unsigned char)(cx | (cy << 2));
+        } else if constexpr (RAT) {
           if (!CENTER) fx = flux_difference_rat((const double*)pc, 1, P.lp, P.lq, sx);
           if (sgn_of(q) != 0) fy = flux_difference_rat((const double*)pc, PT, P.lp, P.lq, sgn_of(q));
         } else {
@@ -125,9 +134,10 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
   }
 }
 
-template <class S, int PRC, bool RAT>
+template <class S, int PRC, bool RAT, bool CODES = false>
 __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
-                                              unsigned int* __restrict__ flag) {
+                                              unsigned int* __restrict__ flag,
+                                              unsigned char* __restrict__ codes = nullptr) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   if (x >= G.Nx || y >= G.Ny) return;
@@ -166,9 +176,11 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
   const float a1f = (float)C.a1;
 
   // ---- phase B: populations, x-node by x-node ----
-  node_update<S, RAT, true>(0, s, d, PL, PT, C, P, a1f);
+  const long long cplane = (long long)G.Nx * G.Ny;
+  unsigned char* cd = CODES ? codes + (long long)y * G.Nx + x : nullptr;
+  node_update<S, RAT, true, CODES>(0, s, d, PL, PT, C, P, a1f, cd, cplane);
 #pragma unroll 1
-  for (int p = 1; p < 5; ++p) node_update<S, RAT, false>(p, s, d, PL, PT, C, P, a1f);
+  for (int p = 1; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, P, a1f, cd, cplane);
 }
 
 template <class S>
@@ -190,6 +202,19 @@ static cudaError_t launch_step_t(const void* src, void* dst, const Geom& G, cons
     if (rat) k_step<S, 0, true><<<grid, block, 0, st>>>(s, d, G, P, flag);
     else k_step<S, 0, false><<<grid, block, 0, st>>>(s, d, G, P, flag);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_codes(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
+                              unsigned char* codes, cudaStream_t st) {
+  if (!(P.lq > 0) || !codes) return cudaErrorInvalidValue;
+  dim3 block(32, 8);
+  dim3 grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
+  const double* s = (const double*)src;
+  double* d = (double*)dst;
+  if (P.prc < 0) k_step<double, -1, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes);
+  else if (P.prc > 0) k_step<double, 1, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes);
+  else k_step<double, 0, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes);
   return cudaGetLastError();
 }
 

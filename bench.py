@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=512, help="oracle sample grid size")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-d2q16", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true")
     return ap.parse_args()
 
 
@@ -300,6 +301,33 @@ def main():
         del sim
         torch.cuda.empty_cache()
 
+    # the paper's shock--vortex case G grid (Sec. III.F: 1680 x 1440 over
+    # [0, 28] x [0, 24], zero-gradient x, periodic y) as a second throughput
+    # workload, both storage forms
+    workloads = {}
+    if not args.no_workloads:
+        sv = inputs.shock_vortex_case("G")
+        sf = [torch.tensor(a) for a in (sv.fields.rho, sv.fields.ux, sv.fields.uy, sv.fields.T)]
+        bcs = [dvbm.ZEROGRAD, dvbm.ZEROGRAD, dvbm.PERIODIC, dvbm.PERIODIC]
+        nx, ny = sv.fields.rho.shape[1], sv.fields.rho.shape[0]
+        wl = {"workload": "shock-vortex case G (Ma_s 1.29, Ma_v 0.39, Re_v 800, Pr 0.75), 1680x1440 over 28x24, "
+                          "zero-gradient x, periodic y, CFL 0.01"}
+        for storage in ("fp64", "fp32dev"):
+            sim = dvbm.Simulation(nx, ny, 0.75, 1.4, sv.mu, bcs=bcs, storage=1 if storage == "fp32dev" else 0,
+                                  Lx=sv.fields.Lx, Ly=sv.fields.Ly, cfl=0.01, check_every=-1)
+            sim.init(*sf)
+            sim.step(args.warmup)
+            torch.cuda.synchronize()
+            barrier()
+            total_ms, _ = timed_steps(sim, args.steps, stream)
+            torch.cuda.synchronize()
+            sim.totals()  # raises if the run went unstable
+            wl[storage] = {"value": nx * ny * args.steps / (total_ms * 1e-3) / 1e6, "unit": "MLUPS",
+                           "ms_per_step": total_ms / args.steps}
+            sim.close()
+        workloads["shock_vortex_G"] = wl
+        torch.cuda.empty_cache()
+
     # end-to-end through the public API with host (pinned) buffers:
     # host fields -> dvbm_init -> K steps -> moments back to host
     e2e = None
@@ -372,6 +400,8 @@ def main():
         t16 = profile_traffic("k_step16")
         line["d2q16_split_I"]["roofline_hbm"]["traffic"] = t16["dram_bytes_per_cell"] * N * N if t16 else None
     line["e2e"] = e2e
+    if workloads:
+        line["workloads"] = workloads
     if not args.no_adjoint:
         line["adjoint"] = adjoint_ratio(dvbm, inputs, torch)
     if not args.no_cpu_baseline:

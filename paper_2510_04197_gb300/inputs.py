@@ -73,10 +73,11 @@ class CouetteSetup:
 
 
 def couette(Nx=4, Ny=256, Ma=0.5, T_C=1.0, T_H=1.2, gamma=1.4, R=1.0, Re=100.0, Ly=1.0,
-            profile="linear", Pr=None) -> CouetteSetup:
+            profile="linear", Pr=None, Ec=None) -> CouetteSetup:
     """Thermal Couette flow (Sec. III.E): bottom wall at rest at T_C, top wall
     moving with u0 = Ma sqrt(gamma R T_C) at T_H; rho = 1/(R T_C);
-    Re = rho u0 Ly / mu; Ec = u0^2 / (C_p (T_H - T_C)).
+    Re = rho u0 Ly / mu; Ec = u0^2 / (C_p (T_H - T_C)).  Given ``Ec``, T_H
+    follows from it (the paper's cases: Ma 0.5 / Ec 4 and Ma 1.2 / Ec 40).
     ``profile="linear"``: linear u and T (the paper's initial condition);
     ``profile="analytic"``: the steady profiles (needs Pr), at uniform pressure."""
     y = _centres(Ny, Ly)[:, None] / Ly + np.zeros((1, Nx))
@@ -84,6 +85,8 @@ def couette(Nx=4, Ny=256, Ma=0.5, T_C=1.0, T_H=1.2, gamma=1.4, R=1.0, Re=100.0, 
     rho_c = 1.0 / (R * T_C)
     mu = rho_c * u0 * Ly / Re
     Cp = gamma * R / (gamma - 1.0)
+    if Ec is not None:
+        T_H = T_C + u0 * u0 / (Cp * Ec)
     Ec = u0 * u0 / (Cp * (T_H - T_C))
     ux = u0 * y
     if profile == "linear":
@@ -110,12 +113,15 @@ class ShockVortexSetup:
 
 
 def shock_vortex(N=1024, Ma_s=1.2, Ma_v=0.25, r_v=0.075, Re_v=800.0, gamma=1.4, R=1.0,
-                 x_s=0.5, x_v=0.35, y_v=0.5, L=1.0) -> ShockVortexSetup:
+                 x_s=0.5, x_v=0.35, y_v=0.5, L=1.0, Ny=None, Ly=None) -> ShockVortexSetup:
     """Stationary normal shock with Rankine--Hugoniot states and an isentropic
-    vortex (Sec. III.F), on a square [0, L]^2.  Pre-shock (left) state
-    rho_l = p_l = 1, u_l = Ma_s c_{s,l}; post-shock state from the jump
-    conditions; vortex of core radius r_v centred at (x_v, y_v) perturbs the
-    local (left or right) state; mu = rho_l c_{s,l} r_v / Re_v."""
+    vortex (Sec. III.F), on [0, L] x [0, Ly] with N x Ny cells (square by
+    default).  Pre-shock (left) state rho_l = p_l = 1, u_l = Ma_s c_{s,l};
+    post-shock state from the jump conditions; vortex of core radius r_v
+    centred at (x_v, y_v) perturbs the local (left or right) state;
+    mu = rho_l c_{s,l} r_v / Re_v."""
+    Ny = N if Ny is None else Ny
+    Ly = L if Ly is None else Ly
     rho_l, p_l = 1.0, 1.0
     cs_l = math.sqrt(gamma * p_l / rho_l)
     u_l = Ma_s * cs_l
@@ -123,8 +129,8 @@ def shock_vortex(N=1024, Ma_s=1.2, Ma_v=0.25, r_v=0.075, Re_v=800.0, gamma=1.4, 
     rho_r = rho_l * (gamma + 1) * M2 / ((gamma - 1) * M2 + 2)
     p_r = p_l * (2 * gamma * M2 - (gamma - 1)) / (gamma + 1)
     u_r = u_l * ((gamma - 1) * M2 + 2) / ((gamma + 1) * M2)
-    x = _centres(N, L)[None, :] + np.zeros((N, 1))
-    y = _centres(N, L)[:, None] + np.zeros((1, N))
+    x = _centres(N, L)[None, :] + np.zeros((Ny, 1))
+    y = _centres(Ny, Ly)[:, None] + np.zeros((1, N))
     left = x <= x_s
     rho_inf = np.where(left, rho_l, rho_r)
     p_inf = np.where(left, p_l, p_r)
@@ -138,7 +144,21 @@ def shock_vortex(N=1024, Ma_s=1.2, Ma_v=0.25, r_v=0.075, Re_v=800.0, gamma=1.4, 
     p = p_inf * base ** (gamma / (gamma - 1))
     T = p / (rho * R)
     mu = rho_l * cs_l * r_v / Re_v
-    return ShockVortexSetup(Fields(rho, ux, uy, T, L, L), mu, cs_l, p_r)
+    return ShockVortexSetup(Fields(rho, ux, uy, T, L, Ly), mu, cs_l, p_r)
+
+
+# Sec. III.F cases of the shock--vortex interaction: (Ma_s, Ma_v)
+SHOCK_VORTEX_CASES = {"C": (1.2, 0.25), "G": (1.29, 0.39)}
+
+
+def shock_vortex_case(case="G", Nx=1680, Ny=1440, gamma=1.4, R=1.0) -> ShockVortexSetup:
+    """The paper's shock--vortex geometry (Sec. III.F): domain [0, 28] x [0, 24],
+    shock at x_s = 8, vortex of radius r_v = 1 centred at (6, 12),
+    Re_v = 800, at the paper's resolution 1680 x 1440 by default (a smaller
+    Nx x Ny keeps dx = dy when Nx/Ny = 28/24)."""
+    Ma_s, Ma_v = SHOCK_VORTEX_CASES[case]
+    return shock_vortex(N=Nx, Ny=Ny, Ma_s=Ma_s, Ma_v=Ma_v, r_v=1.0, Re_v=800.0, gamma=gamma, R=R,
+                        x_s=8.0, x_v=6.0, y_v=12.0, L=28.0, Ly=24.0)
 
 
 def _spectral_field(N: int, rng: np.random.Generator, k_peak=8.0, k_width=2.0, k_max=32):

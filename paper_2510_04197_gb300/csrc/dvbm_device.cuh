@@ -364,14 +364,15 @@ __device__ __forceinline__ double flux_difference_d(const double* __restrict__ p
 // conversions are pure bit manipulation.
 __device__ __forceinline__ int bexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
+// Zero (and subnormal) inputs need no special case: their shift E - e is 63
+// whenever E >= 61, which leaves 0; every caller treats E < 64 as "all values
+// negligible" and returns 0 before using the result.
 __device__ __forceinline__ long long to_block_fixed(double v, int E) {
   const int hi = __double2hiint(v);
   const unsigned lo = (unsigned)__double2loint(v);
   const int e = (hi >> 20) & 0x7ff;
   const unsigned long long m = ((unsigned long long)((unsigned)(hi & 0xfffff) | 0x100000u) << 32) | lo;
-  const int sh = min(E - e, 63);
-  unsigned long long mag = (m << 7) >> sh;
-  mag = e == 0 ? 0ull : mag;  // zero (and subnormal) inputs
+  const unsigned long long mag = (m << 7) >> min(E - e, 63);
   return hi < 0 ? -(long long)mag : (long long)mag;
 }
 
@@ -388,6 +389,124 @@ __device__ __forceinline__ double ll_to_double_scaled(long long F, int scale) {
   const int ex = 1023 + 63 - lz + scale;
   const unsigned hi = (unsigned)(frac >> 32) | ((unsigned)ex << 20) | (F < 0 ? 0x80000000u : 0u);
   return __hiloint2double((int)hi, (int)(unsigned)frac);
+}
+
+// ---- fixed-point Grad expansion (FP64 storage) ----------------------------
+// The expansion t = W W sum C He He /(a! b!) is a fixed linear map of the
+// collision coefficients.  On GB300 the FP64 pipe (2 ops / clock / SM) is the
+// bottleneck of the step, so the expansion runs in block fixed point on the
+// integer pipe: the coefficients of one cell share an exponent (f and g
+// separately) as 60-bit integers, the node constants kh(k, n) (all |kh| < 0.54)
+// are fractions scaled per node to 62-63 bits (kh(k, n) 2^(63 + kd(k)); the
+// outer nodes carry the small weight W_B and gain four bits), each product is
+// the high word of the 128-bit product, and the h values of each x-node are
+// renormalised to 60 bits before the y-expansion.  Truncation stays below
+// 2^-56 of the largest term at each stage; the result is rounded to nearest
+// when it goes back to double, so the collision target carries no
+// systematic bias into the conserved sums.
+__host__ __device__ constexpr int kd(int k) { return k == 0 ? 0 : (k <= 2 ? 1 : 4); }
+__host__ __device__ constexpr long long khfix(int k, int n) {
+  return (long long)(kh(k, n) * 9223372036854775808.0 * (double)(1 << kd(k)));  // exact power-of-two scaling
+}
+
+// int64 -> double rounded to nearest (ties away from zero), value F 2^scale
+__device__ __forceinline__ double ll_to_double_rn(long long F, int scale) {
+  if (F == 0) return 0.0;
+  const unsigned long long mag = F < 0 ? (unsigned long long)(-F) : (unsigned long long)F;
+  const int lz = __clzll(mag);
+  const unsigned long long norm = mag << lz;                     // leading one at bit 63
+  const unsigned long long r = (norm >> 11) + ((norm >> 10) & 1ull);  // 53 or 54 bits after rounding
+  const int carry = (int)(r >> 53);                               // rounding reached 2^53
+  const unsigned long long frac = (r >> carry) & 0x000fffffffffffffull;
+  const int ex = 1023 + 63 - lz + scale + carry;
+  const unsigned hi = (unsigned)(frac >> 32) | ((unsigned)ex << 20) | (F < 0 ? 0x80000000u : 0u);
+  return __hiloint2double((int)hi, (int)(unsigned)frac);
+}
+
+struct CoeffsFix {
+  long long f00, f10, f01, f20, f11, f02, f30, f21, f12, f03, f40, f31, f22, f13, f04;
+  long long g00, g10, g01, g20, g11, g02;
+  int Ef, Eg;  // block exponents: value = X 2^(E - 1082)
+};
+
+__device__ __forceinline__ CoeffsFix coeffs_to_fix(const Coeffs& C) {
+  CoeffsFix X;
+  const int Ef = max(max(max(max(bexp(C.f00), bexp(C.f10)), max(bexp(C.f01), bexp(C.f20))),
+                         max(max(bexp(C.f11), bexp(C.f02)), max(bexp(C.f30), bexp(C.f21)))),
+                     max(max(max(bexp(C.f12), bexp(C.f03)), max(bexp(C.f40), bexp(C.f31))),
+                         max(max(bexp(C.f22), bexp(C.f13)), bexp(C.f04))));
+  const int Eg = max(max(max(bexp(C.g00), bexp(C.g10)), max(bexp(C.g01), bexp(C.g20))),
+                     max(bexp(C.g11), bexp(C.g02)));
+  X.f00 = to_block_fixed(C.f00, Ef); X.f10 = to_block_fixed(C.f10, Ef); X.f01 = to_block_fixed(C.f01, Ef);
+  X.f20 = to_block_fixed(C.f20, Ef); X.f11 = to_block_fixed(C.f11, Ef); X.f02 = to_block_fixed(C.f02, Ef);
+  X.f30 = to_block_fixed(C.f30, Ef); X.f21 = to_block_fixed(C.f21, Ef); X.f12 = to_block_fixed(C.f12, Ef);
+  X.f03 = to_block_fixed(C.f03, Ef); X.f40 = to_block_fixed(C.f40, Ef); X.f31 = to_block_fixed(C.f31, Ef);
+  X.f22 = to_block_fixed(C.f22, Ef); X.f13 = to_block_fixed(C.f13, Ef); X.f04 = to_block_fixed(C.f04, Ef);
+  X.g00 = to_block_fixed(C.g00, Eg); X.g10 = to_block_fixed(C.g10, Eg); X.g01 = to_block_fixed(C.g01, Eg);
+  X.g20 = to_block_fixed(C.g20, Eg); X.g11 = to_block_fixed(C.g11, Eg); X.g02 = to_block_fixed(C.g02, Eg);
+  X.Ef = Ef;
+  X.Eg = Eg;
+  return X;
+}
+
+__device__ __forceinline__ long long mhk(long long x, long long k) { return __mul64hi(x, k); }
+
+// h^b of x-node p (value = h 2^(E - 1081 - kd(p))); k0..k4 = khfix(p, 0..4)
+__device__ __forceinline__ void hfg_fix(const CoeffsFix& X, long long k0, long long k1, long long k2, long long k3,
+                                        long long k4, long long (&hf)[5], long long (&hg)[3]) {
+  hf[0] = mhk(X.f00, k0) + mhk(X.f10, k1) + mhk(X.f20, k2) + mhk(X.f30, k3) + mhk(X.f40, k4);
+  hf[1] = mhk(X.f01, k0) + mhk(X.f11, k1) + mhk(X.f21, k2) + mhk(X.f31, k3);
+  hf[2] = mhk(X.f02, k0) + mhk(X.f12, k1) + mhk(X.f22, k2);
+  hf[3] = mhk(X.f03, k0) + mhk(X.f13, k1);
+  hf[4] = mhk(X.f04, k0);
+  hg[0] = mhk(X.g00, k0) + mhk(X.g10, k1) + mhk(X.g20, k2);
+  hg[1] = mhk(X.g01, k0) + mhk(X.g11, k1);
+  hg[2] = mhk(X.g02, k0);
+}
+// centre node (xi = 0: He_1 = He_3 = 0)
+__device__ __forceinline__ void hfg_fix_centre(const CoeffsFix& X, long long (&hf)[5], long long (&hg)[3]) {
+  constexpr long long k0 = khfix(0, 0), k2 = khfix(0, 2), k4 = khfix(0, 4);
+  hf[0] = mhk(X.f00, k0) + mhk(X.f20, k2) + mhk(X.f40, k4);
+  hf[1] = mhk(X.f01, k0) + mhk(X.f21, k2);
+  hf[2] = mhk(X.f02, k0) + mhk(X.f22, k2);
+  hf[3] = mhk(X.f03, k0);
+  hf[4] = mhk(X.f04, k0);
+  hg[0] = mhk(X.g00, k0) + mhk(X.g20, k2);
+  hg[1] = mhk(X.g01, k0);
+  hg[2] = mhk(X.g02, k0);
+}
+
+// shift the N values so that the largest magnitude has its top bit at 2^60;
+// returns the shift (value of h after the call = h 2^(-sh) of its old scale)
+template <int N>
+__device__ __forceinline__ int renorm_fix(long long (&h)[N]) {
+  unsigned long long m = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) m |= (unsigned long long)(h[i] < 0 ? -h[i] : h[i]);
+  const int sh = m == 0ull ? 0 : __clzll((long long)m) - 3;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    h[i] = sh >= 0 ? (long long)((unsigned long long)h[i] << sh) : (h[i] >> (-sh));
+  return sh;
+}
+
+// y-expansion of one x-node in fixed point, with the +-xi symmetry as in
+// expand_q5 / expand_q3 (value of t_q = t_q 2^(E - 1080 - kd(p) - sh - kd(q)))
+__device__ __forceinline__ void expand_q5_fix(const long long (&h)[5], long long (&t)[5]) {
+  t[0] = mhk(h[0], khfix(0, 0)) + mhk(h[2], khfix(0, 2)) + mhk(h[4], khfix(0, 4));
+  const long long EA = mhk(h[0], khfix(1, 0)) + mhk(h[2], khfix(1, 2)) + mhk(h[4], khfix(1, 4));
+  const long long OA = mhk(h[1], khfix(1, 1)) + mhk(h[3], khfix(1, 3));
+  const long long EB = mhk(h[0], khfix(3, 0)) + mhk(h[2], khfix(3, 2)) + mhk(h[4], khfix(3, 4));
+  const long long OB = mhk(h[1], khfix(3, 1)) + mhk(h[3], khfix(3, 3));
+  t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
+}
+__device__ __forceinline__ void expand_q3_fix(const long long (&h)[3], long long (&t)[5]) {
+  t[0] = mhk(h[0], khfix(0, 0)) + mhk(h[2], khfix(0, 2));
+  const long long EA = mhk(h[0], khfix(1, 0)) + mhk(h[2], khfix(1, 2));
+  const long long OA = mhk(h[1], khfix(1, 1));
+  const long long EB = mhk(h[0], khfix(3, 0)) + mhk(h[2], khfix(3, 2));
+  const long long OB = mhk(h[1], khfix(3, 1));
+  t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
 }
 
 // value of integer F at block exponent E: F 2^(E - 1082)
@@ -434,7 +553,16 @@ __device__ __forceinline__ long long slope_rat(long long Da, long long Db, long 
   return ((Da ^ Db) >= 0) ? (Da >= 0 ? mn : mx) : 0ll;
 }
 
-__device__ __forceinline__ long long to_block_fixed52(double v, int E) { return to_block_fixed(v, E) >> 8; }
+// 52-bit variant: value = X 2^(E - 1074); the magnitude is truncated (toward
+// zero) in one shift of the significand
+__device__ __forceinline__ long long to_block_fixed52(double v, int E) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int e = (hi >> 20) & 0x7ff;
+  const unsigned long long m = ((unsigned long long)((unsigned)(hi & 0xfffff) | 0x100000u) << 32) | lo;
+  const unsigned long long mag = m >> min(E - e + 1, 63);
+  return hi < 0 ? -(long long)mag : (long long)mag;
+}
 
 // returns 4 lq (F_{j+1/2} - F_{j-1/2}) as a double (the caller folds 1/(4 lq))
 __device__ __forceinline__ double flux_difference_rat(const double* __restrict__ ptr, long long stride, int lp,

@@ -4,12 +4,14 @@
 // populations and accumulates the sum-factorised moments; the thread then
 // forms the combined collision coefficients (dvbm_device.cuh).  Phase B walks
 // the populations x-node by x-node: for each it evaluates the collision target
-// (sum-factorised Grad expansion), the upwind-limited flux differences along x
-// and y from the L1-cached neighbours, and writes the new value:
+// (sum-factorised Grad expansion, in block fixed point on the integer pipe),
+// the upwind-limited flux differences along x and y from the L1-cached
+// neighbours, and writes the new value:
 //     F_new = (1 - dt/tau1) F + W W sum C He He - (dt/dx) v_x dF_x - (dt/dy) v_y dF_y.
 // The storage variant FP32DEV keeps float deviations from a reference state;
-// moments, temperature and the equilibrium evaluation stay in double, the
-// advection runs in float on the deviations.
+// moments, temperature and the collision coefficients stay in double, the
+// expansion keeps FP64-or-better precision, the advection runs in float on
+// the deviations.
 #include "dvbm_device.cuh"
 #include "dvbm_internal.h"
 
@@ -37,26 +39,14 @@ __device__ __forceinline__ void load_node(const S* __restrict__ src, long long p
   }
 }
 
-// W_k He_n(xi_k)/n! of the five x-nodes as a constant-bank table, for the
-// node loop below (the same constexpr values the unrolled code folds in).
-__constant__ double c_kh[5][5] = {
-    {kh(0, 0), kh(0, 1), kh(0, 2), kh(0, 3), kh(0, 4)}, {kh(1, 0), kh(1, 1), kh(1, 2), kh(1, 3), kh(1, 4)},
-    {kh(2, 0), kh(2, 1), kh(2, 2), kh(2, 3), kh(2, 4)}, {kh(3, 0), kh(3, 1), kh(3, 2), kh(3, 3), kh(3, 4)},
-    {kh(4, 0), kh(4, 1), kh(4, 2), kh(4, 3), kh(4, 4)}};
-
-// h^b_p of the f and g expansions for a non-central x-node p chosen at run
-// time (same operation order as hf_of<p> / hg_of<p>, p != 0).
-__device__ __forceinline__ void hfg_node(int p, const Coeffs& C, double (&hf)[5], double (&hg)[3]) {
-  const double k0 = c_kh[p][0], k1 = c_kh[p][1], k2 = c_kh[p][2], k3 = c_kh[p][3], k4 = c_kh[p][4];
-  hf[0] = fma(k4, C.f40, fma(k3, C.f30, fma(k2, C.f20, fma(k1, C.f10, k0 * C.f00))));
-  hf[1] = fma(k3, C.f31, fma(k2, C.f21, fma(k1, C.f11, k0 * C.f01)));
-  hf[2] = fma(k2, C.f22, fma(k1, C.f12, k0 * C.f02));
-  hf[3] = fma(k1, C.f13, k0 * C.f03);
-  hf[4] = k0 * C.f04;
-  hg[0] = fma(k2, C.g20, fma(k1, C.g10, k0 * C.g00));
-  hg[1] = fma(k1, C.g11, k0 * C.g01);
-  hg[2] = k0 * C.g02;
-}
+// W_k He_n(xi_k)/n! of the five x-nodes as 63-bit fixed-point fractions
+// (khfix), a constant-bank table for the node loop
+__constant__ long long c_khx[5][5] = {
+    {khfix(0, 0), khfix(0, 1), khfix(0, 2), khfix(0, 3), khfix(0, 4)},
+    {khfix(1, 0), khfix(1, 1), khfix(1, 2), khfix(1, 3), khfix(1, 4)},
+    {khfix(2, 0), khfix(2, 1), khfix(2, 2), khfix(2, 3), khfix(2, 4)},
+    {khfix(3, 0), khfix(3, 1), khfix(3, 2), khfix(3, 3), khfix(3, 4)},
+    {khfix(4, 0), khfix(4, 1), khfix(4, 2), khfix(4, 3), khfix(4, 4)}};
 
 // The ten populations (f and g, y-nodes q = 0..4) of x-node p: collision
 // target from the sum-factorised expansion, upwind-limited flux differences
@@ -67,22 +57,34 @@ __device__ __forceinline__ void hfg_node(int p, const Coeffs& C, double (&hf)[5]
 // CODES (FP64, rational limiter only): also store, per population, the
 // minmod branch codes of the cell's own x and y slopes as one byte
 // (x | y << 2) at cd[pop * cplane]; the adjoint of the step reads them.
+// The expansion runs in block fixed point on the integer pipe from X (the
+// coefficients C converted once per cell), at FP64-or-better precision, for
+// both storage forms.
 template <class S, bool RAT, bool CENTER, bool CODES = false>
 __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* __restrict__ d, long long PL,
-                                            long long PT, const Coeffs& C, const Phys& P, float a1f,
-                                            unsigned char* __restrict__ cd = nullptr, long long cplane = 0) {
+                                            long long PT, const Coeffs& C, const CoeffsFix& X, const Phys& P,
+                                            float a1f, unsigned char* __restrict__ cd = nullptr,
+                                            long long cplane = 0) {
   typedef typename StoreT<S>::adv_t A;
-  double hf[5], tf[5], hg[3], tg[5];
-  if constexpr (CENTER) {
-    hf_of<0>(C, hf);
-    hg_of<0>(C, hg);
-  } else {
-    hfg_node(p, C, hf, hg);
+  double tf[5], tg[5];
+  {
+    long long hf[5], hg[3], xf[5], xg[5];
+    if constexpr (CENTER) hfg_fix_centre(X, hf, hg);
+    else hfg_fix(X, c_khx[p][0], c_khx[p][1], c_khx[p][2], c_khx[p][3], c_khx[p][4], hf, hg);  // p = 0 too
+    const int sf = renorm_fix(hf), sg = renorm_fix(hg);
+    expand_q5_fix(hf, xf);
+    expand_q3_fix(hg, xg);
+    const int dp = (CENTER || p == 0) ? 0 : (p <= 2 ? kd(1) : kd(3));
+    const int scf = X.Ef - 1080 - sf - dp, scg = X.Eg - 1080 - sg - dp;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      tf[q] = X.Ef >= 100 ? ll_to_double_rn(xf[q], scf - kd(q)) : 0.0;
+      tg[q] = X.Eg >= 100 ? ll_to_double_rn(xg[q], scg - kd(q)) : 0.0;
+    }
   }
-  expand_q5(hf, tf);
-  expand_q3(hg, tg);
   // x-node sign and flux factor (p = 1, 3: +xi; p = 2, 4: -xi); warp-uniform selects
   const int sx = (p & 1) ? 1 : -1;
+  const bool xmove = !CENTER && p != 0;  // the centre node has no x-flux
   const int pa = (p + 1) >> 1;  // 1 for p = 1, 2; 2 for p = 3, 4
   double kx = 0.0;
   float kxf = 0.f;
@@ -107,18 +109,18 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
       if constexpr (sizeof(S) == 8) {
         if constexpr (CODES) {
           int cx = 0, cy = 0;
-          if (!CENTER) fx = flux_difference_rat_code((const double*)pc, 1, P.lp, P.lq, sx, cx);
+          if (xmove) fx = flux_difference_rat_code((const double*)pc, 1, P.lp, P.lq, sx, cx);
           if (sgn_of(q) != 0) fy = flux_difference_rat_code((const double*)pc, PT, P.lp, P.lq, sgn_of(q), cy);
           cd[(long long)(5 * p + q + 25 * k) * cplane] = (unsigned char)(cx | (cy << 2));
         } else if constexpr (RAT) {
-          if (!CENTER) fx = flux_difference_rat((const double*)pc, 1, P.lp, P.lq, sx);
+          if (xmove) fx = flux_difference_rat((const double*)pc, 1, P.lp, P.lq, sx);
           if (sgn_of(q) != 0) fy = flux_difference_rat((const double*)pc, PT, P.lp, P.lq, sgn_of(q));
         } else {
-          if (!CENTER) fx = flux_difference_int((const double*)pc, 1, P.hq, sx);
+          if (xmove) fx = flux_difference_int((const double*)pc, 1, P.hq, sx);
           if (sgn_of(q) != 0) fy = flux_difference_int((const double*)pc, PT, P.hq, sgn_of(q));
         }
         double v = fma(C.a1, (double)__ldg(pc), t);
-        if (!CENTER) v = fma(-kx, (double)fx, v);
+        if (xmove) v = fma(-kx, (double)fx, v);
         if (sgn_of(q) != 0) v = fma(RAT ? -P.kyr[q] : -P.kyv[q], (double)fy, v);
         d[co] = (S)v;
       } else {
@@ -174,13 +176,20 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
   // FP32DEV: new deviation = a1 * dev + (t - k1 * ref) - advection, with the
   // bracket (equilibrium evaluation minus the relaxed reference) in double
   const float a1f = (float)C.a1;
+  const CoeffsFix X = coeffs_to_fix(C);
 
   // ---- phase B: populations, x-node by x-node ----
   const long long cplane = (long long)G.Nx * G.Ny;
   unsigned char* cd = CODES ? codes + (long long)y * G.Nx + x : nullptr;
-  node_update<S, RAT, true, CODES>(0, s, d, PL, PT, C, P, a1f, cd, cplane);
+  if constexpr (sizeof(S) == 8) {
+    // one loop body for all five x-nodes (the centre node skips its x-flux)
 #pragma unroll 1
-  for (int p = 1; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, P, a1f, cd, cplane);
+    for (int p = 0; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, X, P, a1f, cd, cplane);
+  } else {
+    node_update<S, RAT, true, CODES>(0, s, d, PL, PT, C, X, P, a1f, cd, cplane);
+#pragma unroll 1
+    for (int p = 1; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, X, P, a1f, cd, cplane);
+  }
 }
 
 template <class S>

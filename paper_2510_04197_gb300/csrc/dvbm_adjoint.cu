@@ -256,6 +256,10 @@ __device__ __forceinline__ void equilibrium_rev(double rho, double ux, double uy
 }
 
 // ------------------------------------------------------- projections / moments
+// kh(k, n) 2^63 for every node (no per-node scaling: the projection sums over
+// nodes at one scale); |kh| < 0.54
+__host__ __device__ constexpr long long c0fix(int k, int n) { return (long long)(kh(k, n) * 9223372036854775808.0); }
+
 // Cbar_ab = sum over the node's populations of lambda W W He_a He_b /(a! b!):
 // accumulate the contribution of x-node p (lf, lg: the 5 f and g values).
 template <int p>
@@ -300,6 +304,65 @@ __device__ __forceinline__ void accumulate_projection(Coeffs& Cb, const double (
   if (p != 0) {
     Cb.g10 = fma(kh(p, 1), gb[0], Cb.g10);
     Cb.g11 = fma(kh(p, 1), gb[1], Cb.g11);
+  }
+}
+
+// The same projection in block fixed point on the integer pipe (the adjoint
+// of the fixed-point expansion of the forward step): lambda of the cell at a
+// shared exponent per f / g (60-bit), node constants kh 2^63, products as
+// high words; the partial sums of all five x-nodes share one scale, so that
+// cbar accumulates across nodes without renormalisation.  Value of cbar_ab:
+// cb 2^(E - 1080).  cb: this thread's 21 accumulators in shared memory (f
+// fields 0..14 in Coeffs order, g fields 15..20, stride 256).
+template <int p>
+__device__ __forceinline__ void accumulate_projection_fix(long long* __restrict__ cb, const double (&lf)[5],
+                                                          const double (&lg)[5], int Ef, int Eg) {
+  long long hb[5];
+  {
+    const long long l0 = to_block_fixed(lf[0], Ef), l1 = to_block_fixed(lf[1], Ef), l2 = to_block_fixed(lf[2], Ef),
+                    l3 = to_block_fixed(lf[3], Ef), l4 = to_block_fixed(lf[4], Ef);
+    const long long sA = l1 + l2, dA = l1 - l2, sB = l3 + l4, dB = l3 - l4;
+    hb[0] = mhk(l0, c0fix(0, 0)) + mhk(sA, c0fix(1, 0)) + mhk(sB, c0fix(3, 0));
+    hb[1] = mhk(dA, c0fix(1, 1)) + mhk(dB, c0fix(3, 1));
+    hb[2] = mhk(l0, c0fix(0, 2)) + mhk(sA, c0fix(1, 2)) + mhk(sB, c0fix(3, 2));
+    hb[3] = mhk(dA, c0fix(1, 3)) + mhk(dB, c0fix(3, 3));
+    hb[4] = mhk(l0, c0fix(0, 4)) + mhk(sA, c0fix(1, 4)) + mhk(sB, c0fix(3, 4));
+  }
+  // field order f00, f10, f01, f20, f11, f02, f30, f21, f12, f03, f40, f31, f22, f13, f04
+  cb[0 * 256] += mhk(hb[0], c0fix(p, 0));
+  cb[2 * 256] += mhk(hb[1], c0fix(p, 0));
+  cb[5 * 256] += mhk(hb[2], c0fix(p, 0));
+  cb[9 * 256] += mhk(hb[3], c0fix(p, 0));
+  cb[14 * 256] += mhk(hb[4], c0fix(p, 0));
+  cb[3 * 256] += mhk(hb[0], c0fix(p, 2));
+  cb[7 * 256] += mhk(hb[1], c0fix(p, 2));
+  cb[12 * 256] += mhk(hb[2], c0fix(p, 2));
+  cb[10 * 256] += mhk(hb[0], c0fix(p, 4));
+  if (p != 0) {
+    cb[1 * 256] += mhk(hb[0], c0fix(p, 1));
+    cb[4 * 256] += mhk(hb[1], c0fix(p, 1));
+    cb[8 * 256] += mhk(hb[2], c0fix(p, 1));
+    cb[13 * 256] += mhk(hb[3], c0fix(p, 1));
+    cb[6 * 256] += mhk(hb[0], c0fix(p, 3));
+    cb[11 * 256] += mhk(hb[1], c0fix(p, 3));
+  }
+  long long gb[3];
+  {
+    const long long l0 = to_block_fixed(lg[0], Eg), l1 = to_block_fixed(lg[1], Eg), l2 = to_block_fixed(lg[2], Eg),
+                    l3 = to_block_fixed(lg[3], Eg), l4 = to_block_fixed(lg[4], Eg);
+    const long long sA = l1 + l2, dA = l1 - l2, sB = l3 + l4, dB = l3 - l4;
+    gb[0] = mhk(l0, c0fix(0, 0)) + mhk(sA, c0fix(1, 0)) + mhk(sB, c0fix(3, 0));
+    gb[1] = mhk(dA, c0fix(1, 1)) + mhk(dB, c0fix(3, 1));
+    gb[2] = mhk(l0, c0fix(0, 2)) + mhk(sA, c0fix(1, 2)) + mhk(sB, c0fix(3, 2));
+  }
+  // g order g00, g10, g01, g20, g11, g02
+  cb[15 * 256] += mhk(gb[0], c0fix(p, 0));
+  cb[17 * 256] += mhk(gb[1], c0fix(p, 0));
+  cb[20 * 256] += mhk(gb[2], c0fix(p, 0));
+  cb[18 * 256] += mhk(gb[0], c0fix(p, 2));
+  if (p != 0) {
+    cb[16 * 256] += mhk(gb[0], c0fix(p, 1));
+    cb[19 * 256] += mhk(gb[1], c0fix(p, 1));
   }
 }
 
@@ -469,6 +532,8 @@ __global__ void __launch_bounds__(256) k_adjoint_local(const double* __restrict_
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   const bool active = x < G.Nx && y < G.Ny;
+  __shared__ long long s_cb[21 * 256];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   ParamBar pb = {0, 0, 0, 0};
   if (active) {
     const long long off = cell_index(G, y, x);
@@ -480,6 +545,16 @@ __global__ void __launch_bounds__(256) k_adjoint_local(const double* __restrict_
     Coeffs Cb = {};
     double a1b = 0.0;
     {
+      // block exponents of the cell's lambda (f and g) for the fixed-point projection
+      int ELf = 0, ELg = 0;
+#pragma unroll 5
+      for (int c = 0; c < 25; ++c) {
+        ELf = max(ELf, bexp(__ldg(ls + c * PL)));
+        ELg = max(ELg, bexp(__ldg(ls + (25 + c) * PL)));
+      }
+      long long* cb = s_cb + tid;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) cb[k * 256] = 0;
       double f[5], g[5], lf[5], lg[5];
 #define DVBM_ADJ_A(p)                                                                  \
       _Pragma("unroll") for (int q = 0; q < 5; ++q) {                                  \
@@ -488,9 +563,19 @@ __global__ void __launch_bounds__(256) k_adjoint_local(const double* __restrict_
         a1b = fma(lf[q], f[q], fma(lg[q], g[q], a1b));                                \
       }                                                                                \
       accumulate_moments<p>(m, f, g);                                                  \
-      accumulate_projection<p>(Cb, lf, lg);
+      accumulate_projection_fix<p>(cb, lf, lg, ELf, ELg);
       DVBM_ADJ_A(0) DVBM_ADJ_A(1) DVBM_ADJ_A(2) DVBM_ADJ_A(3) DVBM_ADJ_A(4)
 #undef DVBM_ADJ_A
+      const bool okf = ELf >= 100, okg = ELg >= 100;
+      const int sf = ELf - 1080, sg = ELg - 1080;
+      auto cv = [](bool ok, long long v, int sc) { return ok ? ll_to_double_rn(v, sc) : 0.0; };
+      Cb.f00 = cv(okf, cb[0 * 256], sf); Cb.f10 = cv(okf, cb[1 * 256], sf); Cb.f01 = cv(okf, cb[2 * 256], sf);
+      Cb.f20 = cv(okf, cb[3 * 256], sf); Cb.f11 = cv(okf, cb[4 * 256], sf); Cb.f02 = cv(okf, cb[5 * 256], sf);
+      Cb.f30 = cv(okf, cb[6 * 256], sf); Cb.f21 = cv(okf, cb[7 * 256], sf); Cb.f12 = cv(okf, cb[8 * 256], sf);
+      Cb.f03 = cv(okf, cb[9 * 256], sf); Cb.f40 = cv(okf, cb[10 * 256], sf); Cb.f31 = cv(okf, cb[11 * 256], sf);
+      Cb.f22 = cv(okf, cb[12 * 256], sf); Cb.f13 = cv(okf, cb[13 * 256], sf); Cb.f04 = cv(okf, cb[14 * 256], sf);
+      Cb.g00 = cv(okg, cb[15 * 256], sg); Cb.g10 = cv(okg, cb[16 * 256], sg); Cb.g01 = cv(okg, cb[17 * 256], sg);
+      Cb.g20 = cv(okg, cb[18 * 256], sg); Cb.g11 = cv(okg, cb[19 * 256], sg); Cb.g02 = cv(okg, cb[20 * 256], sg);
     }
     Moments mb = {};
     const double a1 = collision_coeffs_rev<PRC>(m, P, Cb, a1b, mb, pb);

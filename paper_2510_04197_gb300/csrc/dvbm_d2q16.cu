@@ -198,14 +198,59 @@ __device__ __forceinline__ void write_expansion(double* d, long long PL, const C
 #undef Q16_EXP
 }
 
+// ---- fixed-point expansion (as in dvbm_device.cuh for D2Q25) -------------
+// node constants khq(k, n) 2^(63 + kdq(k)) (|khq| < 0.46; the +-sqrt(3 + sqrt 6)
+// nodes carry the small weight and gain two bits)
+__host__ __device__ constexpr int kdq(int k) { return k < 2 ? 0 : 2; }
+__host__ __device__ constexpr long long khqfix(int k, int n) {
+  return (long long)(khq(k, n) * 9223372036854775808.0 * (double)(1 << kdq(k)));
+}
+struct CoFix {
+  long long f00, f10, f01, f20, f11, f02, f30, f21, f12, f03;
+  long long g00, g10, g01, g20, g11, g02;
+  int Ef, Eg;  // value = X 2^(E - 1082)
+};
+__device__ __forceinline__ CoFix to_fix(const Co& C) {
+  CoFix X;
+  const int Ef = max(max(max(max(bexp(C.f00), bexp(C.f10)), max(bexp(C.f01), bexp(C.f20))),
+                         max(max(bexp(C.f11), bexp(C.f02)), max(bexp(C.f30), bexp(C.f21)))),
+                     max(bexp(C.f12), bexp(C.f03)));
+  const int Eg = max(max(max(bexp(C.g00), bexp(C.g10)), max(bexp(C.g01), bexp(C.g20))),
+                     max(bexp(C.g11), bexp(C.g02)));
+  X.f00 = to_block_fixed(C.f00, Ef); X.f10 = to_block_fixed(C.f10, Ef); X.f01 = to_block_fixed(C.f01, Ef);
+  X.f20 = to_block_fixed(C.f20, Ef); X.f11 = to_block_fixed(C.f11, Ef); X.f02 = to_block_fixed(C.f02, Ef);
+  X.f30 = to_block_fixed(C.f30, Ef); X.f21 = to_block_fixed(C.f21, Ef); X.f12 = to_block_fixed(C.f12, Ef);
+  X.f03 = to_block_fixed(C.f03, Ef);
+  X.g00 = to_block_fixed(C.g00, Eg); X.g10 = to_block_fixed(C.g10, Eg); X.g01 = to_block_fixed(C.g01, Eg);
+  X.g20 = to_block_fixed(C.g20, Eg); X.g11 = to_block_fixed(C.g11, Eg); X.g02 = to_block_fixed(C.g02, Eg);
+  X.Ef = Ef;
+  X.Eg = Eg;
+  return X;
+}
+// t_q = sum_b h^b khq(q, b) with the +-xi symmetry (nodes +a, -a, +b, -b)
+__device__ __forceinline__ void expand_fix(const long long (&h)[4], long long (&t)[4]) {
+  const long long EA = mhk(h[0], khqfix(0, 0)) + mhk(h[2], khqfix(0, 2));
+  const long long OA = mhk(h[1], khqfix(0, 1)) + mhk(h[3], khqfix(0, 3));
+  const long long EB = mhk(h[0], khqfix(2, 0)) + mhk(h[2], khqfix(2, 2));
+  const long long OB = mhk(h[1], khqfix(2, 1)) + mhk(h[3], khqfix(2, 3));
+  t[0] = EA + OA; t[1] = EA - OA; t[2] = EB + OB; t[3] = EB - OB;
+}
+__device__ __forceinline__ void expand3_fix(const long long (&h)[3], long long (&t)[4]) {
+  const long long EA = mhk(h[0], khqfix(0, 0)) + mhk(h[2], khqfix(0, 2));
+  const long long OA = mhk(h[1], khqfix(0, 1));
+  const long long EB = mhk(h[0], khqfix(2, 0)) + mhk(h[2], khqfix(2, 2));
+  const long long OB = mhk(h[1], khqfix(2, 1));
+  t[0] = EA + OA; t[1] = EA - OA; t[2] = EB + OB; t[3] = EB - OB;
+}
+
 }  // namespace q16
 
-// W_k He_n(xi_k)/n! of the four D2Q16 x-nodes as a constant-bank table (the
-// same constexpr values the unrolled helpers fold in), for the node loop.
-__constant__ double c_khq[4][4] = {{q16::khq(0, 0), q16::khq(0, 1), q16::khq(0, 2), q16::khq(0, 3)},
-                                   {q16::khq(1, 0), q16::khq(1, 1), q16::khq(1, 2), q16::khq(1, 3)},
-                                   {q16::khq(2, 0), q16::khq(2, 1), q16::khq(2, 2), q16::khq(2, 3)},
-                                   {q16::khq(3, 0), q16::khq(3, 1), q16::khq(3, 2), q16::khq(3, 3)}};
+// the node constants as a constant-bank table for the node loop
+__constant__ long long c_khqx[4][4] = {
+    {q16::khqfix(0, 0), q16::khqfix(0, 1), q16::khqfix(0, 2), q16::khqfix(0, 3)},
+    {q16::khqfix(1, 0), q16::khqfix(1, 1), q16::khqfix(1, 2), q16::khqfix(1, 3)},
+    {q16::khqfix(2, 0), q16::khqfix(2, 1), q16::khqfix(2, 2), q16::khqfix(2, 3)},
+    {q16::khqfix(3, 0), q16::khqfix(3, 1), q16::khqfix(3, 2), q16::khqfix(3, 3)}};
 
 template <int PRC, bool RAT>
 __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, double* __restrict__ dst, Geom G,
@@ -221,23 +266,45 @@ __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, 
   const Mom m = cell_moments(s, PL);
   const Co C = coeffs<PRC>(m, P);
   if (C.bad) atomicOr(flag, 1u);
+  // fixed-point coefficients in shared memory (field k of thread t at
+  // [k * 256 + t]) rather than in 32 registers across the node loop
+  __shared__ long long s_fix[16 * 256];
+  long long* xs = s_fix + threadIdx.y * 32 + threadIdx.x;
+  int Ef, Eg;
+  {
+    const CoFix Xr = to_fix(C);
+    const long long v[16] = {Xr.f00, Xr.f10, Xr.f01, Xr.f20, Xr.f11, Xr.f02, Xr.f30, Xr.f21,
+                             Xr.f12, Xr.f03, Xr.g00, Xr.g10, Xr.g01, Xr.g20, Xr.g11, Xr.g02};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) xs[k * 256] = v[k];
+    Ef = Xr.Ef;
+    Eg = Xr.Eg;
+  }
   // x-nodes p = 0..3 in a run-time loop (one copy of the body: the kernel
   // stays small enough for the instruction cache); the y-nodes are unrolled.
+  // The Grad expansion runs in block fixed point on the integer pipe.
 #pragma unroll 1
   for (int p = 0; p < 4; ++p) {
-    const double k0 = c_khq[p][0], k1 = c_khq[p][1], k2 = c_khq[p][2], k3 = c_khq[p][3];
-    double h[4], tf[4], hh[4], tg[4];
-    // same operation order as hf<p> / hg<p>
-    h[0] = fma(k3, C.f30, fma(k2, C.f20, fma(k1, C.f10, k0 * C.f00)));
-    h[1] = fma(k2, C.f21, fma(k1, C.f11, k0 * C.f01));
-    h[2] = fma(k1, C.f12, k0 * C.f02);
-    h[3] = k0 * C.f03;
-    hh[0] = fma(k2, C.g20, fma(k1, C.g10, k0 * C.g00));
-    hh[1] = fma(k1, C.g11, k0 * C.g01);
-    hh[2] = k0 * C.g02;
-    hh[3] = 0.0;
-    expand(h, tf);
-    expand(hh, tg);
+    const long long k0 = c_khqx[p][0], k1 = c_khqx[p][1], k2 = c_khqx[p][2], k3 = c_khqx[p][3];
+    long long h[4], hh[3], xf[4], xg[4];
+    h[0] = mhk(xs[0 * 256], k0) + mhk(xs[1 * 256], k1) + mhk(xs[3 * 256], k2) + mhk(xs[6 * 256], k3);
+    h[1] = mhk(xs[2 * 256], k0) + mhk(xs[4 * 256], k1) + mhk(xs[7 * 256], k2);
+    h[2] = mhk(xs[5 * 256], k0) + mhk(xs[8 * 256], k1);
+    h[3] = mhk(xs[9 * 256], k0);
+    hh[0] = mhk(xs[10 * 256], k0) + mhk(xs[11 * 256], k1) + mhk(xs[13 * 256], k2);
+    hh[1] = mhk(xs[12 * 256], k0) + mhk(xs[14 * 256], k1);
+    hh[2] = mhk(xs[15 * 256], k0);
+    const int sf = renorm_fix(h), sg = renorm_fix(hh);
+    expand_fix(h, xf);
+    expand3_fix(hh, xg);
+    const int dp = kdq(p < 2 ? 0 : 2);
+    double tf[4], tg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // value of t_q = x 2^(E - 1080 - kdq(p) - s - kdq(q))
+      tf[q] = Ef >= 100 ? ll_to_double_rn(xf[q], Ef - 1080 - dp - sf - kdq(q)) : 0.0;
+      tg[q] = Eg >= 100 ? ll_to_double_rn(xg[q], Eg - 1080 - dp - sg - kdq(q)) : 0.0;
+    }
     const int sx = (p & 1) ? -1 : 1;  // nodes +a, -a, +b, -b
     // kx of node p: kxv[1] = -kxv[0] and kxv[3] = -kxv[2] exactly
     const double kb = p < 2 ? (RAT ? P.kxr[0] : P.kxv[0]) : (RAT ? P.kxr[2] : P.kxv[2]);

@@ -48,6 +48,45 @@ __constant__ long long c_khx[5][5] = {
     {khfix(3, 0), khfix(3, 1), khfix(3, 2), khfix(3, 3), khfix(3, 4)},
     {khfix(4, 0), khfix(4, 1), khfix(4, 2), khfix(4, 3), khfix(4, 4)}};
 
+// This thread's fixed-point collision coefficients, kept in shared memory
+// (field k of thread t at [k * 256 + t]: consecutive threads, consecutive
+// words) rather than in 42 registers across the node loop, so that three
+// CTAs fit on an SM.  Field order as in CoeffsFix.
+constexpr int kFixFields = 21;
+struct FixView {
+  const long long* b;
+  __device__ __forceinline__ long long operator()(int k) const { return b[k * 256]; }
+};
+__device__ __forceinline__ void fix_to_smem(const CoeffsFix& X, long long* b) {
+  const long long v[kFixFields] = {X.f00, X.f10, X.f01, X.f20, X.f11, X.f02, X.f30, X.f21, X.f12, X.f03, X.f40,
+                                   X.f31, X.f22, X.f13, X.f04, X.g00, X.g10, X.g01, X.g20, X.g11, X.g02};
+#pragma unroll
+  for (int k = 0; k < kFixFields; ++k) b[k * 256] = v[k];
+}
+// h^b of x-node p from the shared-memory coefficients (hfg_fix / hfg_fix_centre)
+__device__ __forceinline__ void hfg_fix_view(const FixView& X, long long k0, long long k1, long long k2, long long k3,
+                                             long long k4, long long (&hf)[5], long long (&hg)[3]) {
+  hf[0] = mhk(X(0), k0) + mhk(X(1), k1) + mhk(X(3), k2) + mhk(X(6), k3) + mhk(X(10), k4);
+  hf[1] = mhk(X(2), k0) + mhk(X(4), k1) + mhk(X(7), k2) + mhk(X(11), k3);
+  hf[2] = mhk(X(5), k0) + mhk(X(8), k1) + mhk(X(12), k2);
+  hf[3] = mhk(X(9), k0) + mhk(X(13), k1);
+  hf[4] = mhk(X(14), k0);
+  hg[0] = mhk(X(15), k0) + mhk(X(16), k1) + mhk(X(18), k2);
+  hg[1] = mhk(X(17), k0) + mhk(X(19), k1);
+  hg[2] = mhk(X(20), k0);
+}
+__device__ __forceinline__ void hfg_fix_view_centre(const FixView& X, long long (&hf)[5], long long (&hg)[3]) {
+  constexpr long long k0 = khfix(0, 0), k2 = khfix(0, 2), k4 = khfix(0, 4);
+  hf[0] = mhk(X(0), k0) + mhk(X(3), k2) + mhk(X(10), k4);
+  hf[1] = mhk(X(2), k0) + mhk(X(7), k2);
+  hf[2] = mhk(X(5), k0) + mhk(X(12), k2);
+  hf[3] = mhk(X(9), k0);
+  hf[4] = mhk(X(14), k0);
+  hg[0] = mhk(X(15), k0) + mhk(X(18), k2);
+  hg[1] = mhk(X(17), k0);
+  hg[2] = mhk(X(20), k0);
+}
+
 // The ten populations (f and g, y-nodes q = 0..4) of x-node p: collision
 // target from the sum-factorised expansion, upwind-limited flux differences
 // along x (p != 0) and y (q != 0), new value.  CENTER: p = 0 (xi_x = 0, no
@@ -62,24 +101,25 @@ __constant__ long long c_khx[5][5] = {
 // both storage forms.
 template <class S, bool RAT, bool CENTER, bool CODES = false>
 __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* __restrict__ d, long long PL,
-                                            long long PT, const Coeffs& C, const CoeffsFix& X, const Phys& P,
+                                            long long PT, const Coeffs& C, const FixView& X, int Ef, int Eg,
+                                            const Phys& P,
                                             float a1f, unsigned char* __restrict__ cd = nullptr,
                                             long long cplane = 0) {
   typedef typename StoreT<S>::adv_t A;
   double tf[5], tg[5];
   {
     long long hf[5], hg[3], xf[5], xg[5];
-    if constexpr (CENTER) hfg_fix_centre(X, hf, hg);
-    else hfg_fix(X, c_khx[p][0], c_khx[p][1], c_khx[p][2], c_khx[p][3], c_khx[p][4], hf, hg);  // p = 0 too
+    if constexpr (CENTER) hfg_fix_view_centre(X, hf, hg);
+    else hfg_fix_view(X, c_khx[p][0], c_khx[p][1], c_khx[p][2], c_khx[p][3], c_khx[p][4], hf, hg);  // p = 0 too
     const int sf = renorm_fix(hf), sg = renorm_fix(hg);
     expand_q5_fix(hf, xf);
     expand_q3_fix(hg, xg);
     const int dp = (CENTER || p == 0) ? 0 : (p <= 2 ? kd(1) : kd(3));
-    const int scf = X.Ef - 1080 - sf - dp, scg = X.Eg - 1080 - sg - dp;
+    const int scf = Ef - 1080 - sf - dp, scg = Eg - 1080 - sg - dp;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      tf[q] = X.Ef >= 100 ? ll_to_double_rn(xf[q], scf - kd(q)) : 0.0;
-      tg[q] = X.Eg >= 100 ? ll_to_double_rn(xg[q], scg - kd(q)) : 0.0;
+      tf[q] = Ef >= 100 ? ll_to_double_rn(xf[q], scf - kd(q)) : 0.0;
+      tg[q] = Eg >= 100 ? ll_to_double_rn(xg[q], scg - kd(q)) : 0.0;
     }
   }
   // x-node sign and flux factor (p = 1, 3: +xi; p = 2, 4: -xi); warp-uniform selects
@@ -176,7 +216,16 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
   // FP32DEV: new deviation = a1 * dev + (t - k1 * ref) - advection, with the
   // bracket (equilibrium evaluation minus the relaxed reference) in double
   const float a1f = (float)C.a1;
-  const CoeffsFix X = coeffs_to_fix(C);
+  __shared__ long long s_fix[kFixFields * 256];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  int Ef, Eg;
+  {
+    const CoeffsFix Xr = coeffs_to_fix(C);
+    fix_to_smem(Xr, s_fix + tid);
+    Ef = Xr.Ef;
+    Eg = Xr.Eg;
+  }
+  const FixView X{s_fix + tid};
 
   // ---- phase B: populations, x-node by x-node ----
   const long long cplane = (long long)G.Nx * G.Ny;
@@ -184,11 +233,11 @@ __global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __re
   if constexpr (sizeof(S) == 8) {
     // one loop body for all five x-nodes (the centre node skips its x-flux)
 #pragma unroll 1
-    for (int p = 0; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, X, P, a1f, cd, cplane);
+    for (int p = 0; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, X, Ef, Eg, P, a1f, cd, cplane);
   } else {
-    node_update<S, RAT, true, CODES>(0, s, d, PL, PT, C, X, P, a1f, cd, cplane);
+    node_update<S, RAT, true, CODES>(0, s, d, PL, PT, C, X, Ef, Eg, P, a1f, cd, cplane);
 #pragma unroll 1
-    for (int p = 1; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, X, P, a1f, cd, cplane);
+    for (int p = 1; p < 5; ++p) node_update<S, RAT, false, CODES>(p, s, d, PL, PT, C, X, Ef, Eg, P, a1f, cd, cplane);
   }
 }
 

@@ -526,7 +526,7 @@ __device__ __forceinline__ double advection_adjoint_rat(const double* __restrict
 // state X; per-block sums of the parameter adjoints (dt_mu, Pr, gm1, epsf)
 // into partial[blk*4 + k].
 template <int PRC>
-__global__ void __launch_bounds__(256) k_adjoint_local(const double* __restrict__ X, const double* __restrict__ Lin,
+__global__ void __launch_bounds__(256, 2) k_adjoint_local(const double* __restrict__ X, const double* __restrict__ Lin,
                                                        double* __restrict__ Lout, double* __restrict__ partial,
                                                        Geom G, Phys P) {
   const int x = blockIdx.x * 32 + threadIdx.x;

@@ -33,7 +33,11 @@ BYTES_PER_CELL = {"fp64": 2 * 50 * 8, "fp32dev": 2 * 50 * 4, "d2q16": 2 * 32 * 8
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM_GBS = 6800.0
-NOMINAL_FP64_TFLOPS = 1.25  # profiling recipe: GB300 FP64 (FMA = 2 flops)
+# GB300 unit counts and clock (profiling recipe): 152 SMs, 2.07 GHz; FP64 at 2
+# instructions per clock per SM (FMA = 2 flops); 4 warp schedulers per SM,
+# one warp instruction per scheduler per clock
+NOMINAL_FP64_TFLOPS = 152 * 2 * 2.07e9 * 2 / 1e12          # 1.259
+NOMINAL_ISSUE_GWARPINST = 152 * 4 * 2.07e9 / 1e9            # 1258.6 G warp instructions / s
 
 
 def parse():
@@ -372,7 +376,15 @@ def main():
         roofline = {"bound": "alu", "achieved": ach_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach_tf / NOMINAL_FP64_TFLOPS, "traffic": roofline_hbm["traffic"],
                     "what": "FP64 pipe: executed FP64 flops per cell (ncu instruction mix, FMA = 2) / step-kernel time; "
-                            "peak = nominal GB300 FP64 1.25 TFLOP/s"}
+                            "peak = 152 SMs x 2 FP64 inst/clk x 2.07 GHz x 2"}
+        if tr.get("thread_inst_per_cell"):
+            # the step also runs its advection and Grad expansion on the integer
+            # pipe, so the issue slots are the second ceiling
+            ach_is = tr["thread_inst_per_cell"] / 32.0 * N * N / (r64["kernel_ms"] * 1e-3) / 1e9
+            roofline["issue"] = {"achieved": ach_is, "peak": NOMINAL_ISSUE_GWARPINST,
+                                 "unit": "G warp-instructions/s", "frac": ach_is / NOMINAL_ISSUE_GWARPINST,
+                                 "what": "all executed instructions (ncu) per cell / 32 x cells / step-kernel time; "
+                                         "peak = 152 SMs x 4 schedulers x 2.07 GHz"}
     else:
         roofline = dict(roofline_hbm)
     line = {"metric": "MLUPS", "value": r64["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,

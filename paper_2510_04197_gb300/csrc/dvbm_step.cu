@@ -177,7 +177,7 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
 }
 
 template <class S, int PRC, bool RAT, bool CODES = false>
-__global__ void __launch_bounds__(256) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
+__global__ void __launch_bounds__(256, 4) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
                                               unsigned int* __restrict__ flag,
                                               unsigned char* __restrict__ codes = nullptr) {
   const int x = blockIdx.x * 32 + threadIdx.x;

@@ -55,8 +55,10 @@ typedef enum { DVBM_D2Q25_SPLIT_II = 0, DVBM_D2Q16_SPLIT_I = 1 } dvbm_lattice;
 
 /* Population storage.  FP64: populations as doubles.  FP32DEV: populations
  * stored as float deviations from w_i rho0 (f) and w_i rho0 (C_v - R) T0 (g);
- * moments, temperature and equilibria are evaluated in double, advection in
- * float on the deviations. */
+ * moments, temperature and the collision coefficients are evaluated in
+ * double, the Grad expansion of the collision target at FP64-or-better
+ * precision (block fixed point, as for FP64 storage), advection in float on
+ * the deviations. */
 typedef enum { DVBM_FP64 = 0, DVBM_FP32DEV = 1 } dvbm_storage;
 
 /* Boundary kinds (Sec. III.A.3, Sec. III.E).  PERIODIC: wrap (must be set on

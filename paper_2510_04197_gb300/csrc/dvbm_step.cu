@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(256, 4) k_step(const S* __restrict__ src, S* _
     C.g00 -= C.k1 * P.gref0;
   }
   // FP32DEV: new deviation = a1 * dev + (t - k1 * ref) - advection, with the
-  // bracket (equilibrium evaluation minus the relaxed reference) in double
+  // bracket (equilibrium evaluation minus the relaxed reference) at
+  // FP64-or-better precision, rounded to float only in the update
   const float a1f = (float)C.a1;
   __shared__ long long s_fix[kFixFields * 256];
   const int tid = threadIdx.y * 32 + threadIdx.x;

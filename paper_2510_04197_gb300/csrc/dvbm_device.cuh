@@ -509,6 +509,36 @@ __device__ __forceinline__ void expand_q3_fix(const long long (&h)[3], long long
   t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
 }
 
+// int64 -> float rounded to nearest (ties away from zero), value F 2^scale;
+// results below the normal float range flush to zero
+__device__ __forceinline__ float ll_to_float_rn(long long F, int scale) {
+  if (F == 0) return 0.0f;
+  const unsigned long long mag = F < 0 ? (unsigned long long)(-F) : (unsigned long long)F;
+  const int lz = __clzll(mag);
+  const unsigned long long norm = mag << lz;                          // leading one at bit 63
+  const unsigned r = (unsigned)(norm >> 40) + (unsigned)((norm >> 39) & 1ull);  // 24 or 25 bits
+  const int carry = (int)(r >> 24);
+  const unsigned frac = (r >> carry) & 0x7fffffu;
+  const int ex = 127 + 63 - lz + scale + carry;
+  if (ex <= 0) return 0.0f;
+  return __uint_as_float((unsigned)min(ex, 255) << 23 | (ex >= 255 ? 0u : frac) | (F < 0 ? 0x80000000u : 0u));
+}
+
+// float -> double by bit manipulation (exact; the hardware conversion runs on
+// the FP64 pipe on GB300).  Zero and subnormal floats give a signed zero;
+// infinities and NaNs keep their class.
+__device__ __forceinline__ double f2d_bits(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned sign = u & 0x80000000u;
+  const unsigned m = u & 0x7fffffu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // value of integer F at block exponent E: F 2^(E - 1082)
 __device__ __forceinline__ double from_block_fixed(long long F, int E) {
   if (E < 64) return 0.0;

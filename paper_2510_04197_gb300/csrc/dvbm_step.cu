@@ -33,8 +33,8 @@ __device__ __forceinline__ void load_node(const S* __restrict__ src, long long p
       f[q] = __ldg(src + c * plane);
       g[q] = __ldg(src + (25 + c) * plane);
     } else {
-      f[q] = (double)__ldg(src + c * plane);
-      g[q] = (double)__ldg(src + (25 + c) * plane);
+      f[q] = f2d_bits(__ldg(src + c * plane));
+      g[q] = f2d_bits(__ldg(src + (25 + c) * plane));
     }
   }
 }
@@ -106,7 +106,9 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
                                             float a1f, unsigned char* __restrict__ cd = nullptr,
                                             long long cplane = 0) {
   typedef typename StoreT<S>::adv_t A;
-  double tf[5], tg[5];
+  // collision target in the storage's arithmetic type (FP32-deviation storage
+  // rounds the fixed-point result straight to float)
+  A tf[5], tg[5];
   {
     long long hf[5], hg[3], xf[5], xg[5];
     if constexpr (CENTER) hfg_fix_view_centre(X, hf, hg);
@@ -118,8 +120,13 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
     const int scf = Ef - 1080 - sf - dp, scg = Eg - 1080 - sg - dp;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      tf[q] = Ef >= 100 ? ll_to_double_rn(xf[q], scf - kd(q)) : 0.0;
-      tg[q] = Eg >= 100 ? ll_to_double_rn(xg[q], scg - kd(q)) : 0.0;
+      if constexpr (sizeof(S) == 8) {
+        tf[q] = Ef >= 100 ? ll_to_double_rn(xf[q], scf - kd(q)) : 0.0;
+        tg[q] = Eg >= 100 ? ll_to_double_rn(xg[q], scg - kd(q)) : 0.0;
+      } else {
+        tf[q] = Ef >= 100 ? ll_to_float_rn(xf[q], scf - kd(q)) : 0.0f;
+        tg[q] = Eg >= 100 ? ll_to_float_rn(xg[q], scg - kd(q)) : 0.0f;
+      }
     }
   }
   // x-node sign and flux factor (p = 1, 3: +xi; p = 2, 4: -xi); warp-uniform selects
@@ -144,7 +151,7 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
     for (int k = 0; k < 2; ++k) {
       const long long co = pbase + (long long)(q + 25 * k) * PL;
       const S* pc = s + co;
-      const double t = k == 0 ? tf[q] : tg[q];
+      const A t = k == 0 ? tf[q] : tg[q];
       A fx = 0, fy = 0;
       if constexpr (sizeof(S) == 8) {
         if constexpr (CODES) {
@@ -170,7 +177,7 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
         float adv = 0.f;
         if (!CENTER) adv = kxf * (float)fx;
         if (sgn_of(q) != 0) adv = fmaf(P.kyvf[q], (float)fy, adv);
-        d[co] = (S)(fmaf(a1f, (float)__ldg(pc), __double2float_rn(t)) - adv);
+        d[co] = (S)(fmaf(a1f, (float)__ldg(pc), t) - adv);
       }
     }
   }

@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-d2q16", action="store_true")
     ap.add_argument("--no-workloads", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="throughput sweep over grid size, rms Mach number and storage form (one JSON line)")
     return ap.parse_args()
 
 
@@ -245,8 +247,46 @@ def timed_steps(sim, K, stream):
     return evs[0].elapsed_time(evs[K]), per
 
 
+def run_sweep(args):
+    """Throughput sweep of the periodic multimode workload: N^2 for N in
+    {1024, 2048, 4096}, rms Ma in {0.3, 0.6, 1.2}, FP64 and FP32-deviation
+    storage; --steps timed steps (default 500 here) after --warmup.  A run
+    that trips the instability flag is reported with the step count reached
+    (the static lattices have a Mach limit)."""
+    import torch
+    from paper_2510_04197_gb300 import dvbm, inputs
+    steps = args.steps if args.steps != 20 else 500
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N in (1024, 2048, 4096):
+        for ma in (0.3, 0.6, 1.2):
+            F = inputs.multimode(N, seed=0, rms_Ma=ma)
+            fields = [torch.tensor(a) for a in (F.rho, F.ux, F.uy, F.T)]
+            for storage in ("fp64", "fp32dev"):
+                row = {"grid": N, "rms_Ma": ma, "storage": storage}
+                sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, storage=1 if storage == "fp32dev" else 0,
+                                      check_every=-1)
+                try:
+                    sim.init(*fields)
+                    sim.step(args.warmup)
+                    torch.cuda.synchronize()
+                    total_ms, _ = timed_steps(sim, steps, stream)
+                    sim.totals()  # raises if the run went unstable
+                    row.update({"mlups": N * N * steps / (total_ms * 1e-3) / 1e6, "steps": steps,
+                                "ms_per_step": total_ms / steps})
+                except Exception as e:  # instability flag or bad state
+                    row.update({"unstable": str(e).splitlines()[0][:160], "steps_reached": sim.steps})
+                sim.close()
+                rows.append(row)
+                torch.cuda.empty_cache()
+    print(json.dumps({"sweep": rows, "workload": "periodic multimode, Pr 0.71, gamma 1.4, mu 5e-5, CFL 0.01",
+                      "unit": "MLUPS"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.sweep:
+        return run_sweep(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -150,3 +150,31 @@ def test_shock_vortex_case_G_paper_resolution_runs(D):
     for k in ("rho", "ux", "uy", "T"):
         assert np.isfinite(g[k]).all(), k
     assert g["rho"].min() > 0.9 * F.rho.min() and g["rho"].max() < 1.1 * F.rho.max()
+
+
+def test_shock_vortex_1024_fp64_vs_fp32_deviation_4000_steps(D):
+    """The square shock--vortex workload at full size (1024^2, Ma_s = 1.2,
+    Ma_v = 0.25, r_v = 0.075 L, Re_v = 800, Pr = 0.75, zero-gradient x,
+    periodic y, CFL 0.01, 4000 steps) in both storage forms: both stay
+    stable; the FP32-deviation fields are within relative L1 1e-4 of FP64
+    across the shock; the change of the totals (mass and energy flow through
+    the open x-boundaries) agrees between the forms to 1e-6 of the totals."""
+    N, n = 1024, 4000
+    sv = I.shock_vortex(N=N)
+    F = sv.fields
+    bcs = [D.ZEROGRAD, D.ZEROGRAD, D.PERIODIC, D.PERIODIC]
+    out, drift = {}, {}
+    for st in (0, 1):
+        sim = D.Simulation(N, N, 0.75, 1.4, sv.mu, bcs=bcs, storage=st, cfl=0.01)
+        sim.init(*(torch.tensor(a) for a in (F.rho, F.ux, F.uy, F.T)))
+        t0 = np.array(sim.totals())
+        sim.step(n)
+        t1 = np.array(sim.totals())
+        out[st] = {k: v.cpu().numpy() for k, v in sim.moments().items()}
+        drift[st] = (t1 - t0) / np.abs(t0).clip(min=1e-300)
+        sim.close()
+    for k in ("rho", "T"):
+        l1 = np.abs(out[1][k] - out[0][k]).sum() / np.abs(out[0][k]).sum()
+        assert l1 < 1e-4, (k, l1)
+    for i in (0, 3):  # mass, total energy
+        assert abs(drift[1][i] - drift[0][i]) < 1e-6, (i, drift[0][i], drift[1][i])

@@ -310,10 +310,10 @@ __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, 
     const double kb = p < 2 ? (RAT ? P.kxr[0] : P.kxv[0]) : (RAT ? P.kxr[2] : P.kxv[2]);
     const double kx = kb * (double)sx;
     const long long pbase = (long long)(4 * p) * PL;
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
+      for (int q = 0; q < 4; ++q) {
         const long long co = pbase + (long long)(q + 16 * k) * PL;
         const double* pc = s + co;
         double fx, fy;

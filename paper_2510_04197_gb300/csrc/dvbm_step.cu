@@ -145,10 +145,10 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
   }
   const A hb = (A)P.hb;
   const long long pbase = (long long)(5 * p) * PL;
+#pragma unroll 1
+  for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int q = 0; q < 5; ++q) {
       const long long co = pbase + (long long)(q + 25 * k) * PL;
       const S* pc = s + co;
       const A t = k == 0 ? tf[q] : tg[q];

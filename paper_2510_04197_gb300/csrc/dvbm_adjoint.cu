@@ -525,10 +525,12 @@ __device__ __forceinline__ double advection_adjoint_rat(const double* __restrict
 // k_adjoint_local: Lout = a1 Lin + sum_j mbar_j dm_j/dX (collision part) at
 // state X; per-block sums of the parameter adjoints (dt_mu, Pr, gm1, epsf)
 // into partial[blk*4 + k].
-template <int PRC>
+// MOMS: the moments of X come from the recompute step (moms[k][y][x], the
+// same sums in the same order) instead of being summed again here.
+template <int PRC, bool MOMS>
 __global__ void __launch_bounds__(256, 2) k_adjoint_local(const double* __restrict__ X, const double* __restrict__ Lin,
                                                        double* __restrict__ Lout, double* __restrict__ partial,
-                                                       Geom G, Phys P) {
+                                                       const double* __restrict__ moms, Geom G, Phys P) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   const bool active = x < G.Nx && y < G.Ny;
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_local(const double* __restri
         lf[q] = __ldg(ls + (5 * p + q) * PL); lg[q] = __ldg(ls + (25 + 5 * p + q) * PL); \
         a1b = fma(lf[q], f[q], fma(lg[q], g[q], a1b));                                \
       }                                                                                \
-      accumulate_moments<p>(m, f, g);                                                  \
+      if (!MOMS) accumulate_moments<p>(m, f, g);                                       \
       accumulate_projection_fix<p>(cb, lf, lg, ELf, ELg);
       DVBM_ADJ_A(0) DVBM_ADJ_A(1) DVBM_ADJ_A(2) DVBM_ADJ_A(3) DVBM_ADJ_A(4)
 #undef DVBM_ADJ_A
@@ -576,6 +578,14 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_local(const double* __restri
       Cb.f22 = cv(okf, cb[12 * 256], sf); Cb.f13 = cv(okf, cb[13 * 256], sf); Cb.f04 = cv(okf, cb[14 * 256], sf);
       Cb.g00 = cv(okg, cb[15 * 256], sg); Cb.g10 = cv(okg, cb[16 * 256], sg); Cb.g01 = cv(okg, cb[17 * 256], sg);
       Cb.g20 = cv(okg, cb[18 * 256], sg); Cb.g11 = cv(okg, cb[19 * 256], sg); Cb.g02 = cv(okg, cb[20 * 256], sg);
+    }
+    if (MOMS) {
+      const long long cp = (long long)G.Nx * G.Ny, ci = (long long)y * G.Nx + x;
+      m.m00 = moms[0 * cp + ci]; m.m10 = moms[1 * cp + ci]; m.m01 = moms[2 * cp + ci];
+      m.m20 = moms[3 * cp + ci]; m.m11 = moms[4 * cp + ci]; m.m02 = moms[5 * cp + ci];
+      m.m30 = moms[6 * cp + ci]; m.m21 = moms[7 * cp + ci]; m.m12 = moms[8 * cp + ci];
+      m.m03 = moms[9 * cp + ci]; m.g00 = moms[10 * cp + ci]; m.g10 = moms[11 * cp + ci];
+      m.g01 = moms[12 * cp + ci];
     }
     Moments mb = {};
     const double a1 = collision_coeffs_rev<PRC>(m, P, Cb, a1b, mb, pb);
@@ -737,11 +747,18 @@ __global__ void __launch_bounds__(256) k_adjoint_init(const double* __restrict__
 int adjoint_blocks(const Geom& G) { return ((G.Nx + 31) / 32) * ((G.Ny + 7) / 8); }
 
 cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial,
-                                const unsigned char* codes, const Geom& G, const Phys& P, cudaStream_t st) {
+                                const unsigned char* codes, const double* moms, const Geom& G, const Phys& P,
+                                cudaStream_t st) {
   dim3 block(32, 8), grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
-  if (P.prc < 0) k_adjoint_local<-1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
-  else if (P.prc > 0) k_adjoint_local<1><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
-  else k_adjoint_local<0><<<grid, block, 0, st>>>(X, Lin, Lout, partial, G, P);
+  if (moms) {
+    if (P.prc < 0) k_adjoint_local<-1, true><<<grid, block, 0, st>>>(X, Lin, Lout, partial, moms, G, P);
+    else if (P.prc > 0) k_adjoint_local<1, true><<<grid, block, 0, st>>>(X, Lin, Lout, partial, moms, G, P);
+    else k_adjoint_local<0, true><<<grid, block, 0, st>>>(X, Lin, Lout, partial, moms, G, P);
+  } else {
+    if (P.prc < 0) k_adjoint_local<-1, false><<<grid, block, 0, st>>>(X, Lin, Lout, partial, nullptr, G, P);
+    else if (P.prc > 0) k_adjoint_local<1, false><<<grid, block, 0, st>>>(X, Lin, Lout, partial, nullptr, G, P);
+    else k_adjoint_local<0, false><<<grid, block, 0, st>>>(X, Lin, Lout, partial, nullptr, G, P);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid3(grid.x, grid.y, NPOP);

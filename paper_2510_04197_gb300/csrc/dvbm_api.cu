@@ -510,6 +510,7 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
   std::vector<void*> seg;
   double* part = nullptr;
   unsigned char* codes = nullptr;
+  double* moms = nullptr;  // the moments of each recomputed state (13 doubles per cell and step)
   const long long nslots = (n + 2) * (long long)nblk * 4;
   const size_t code_step = (size_t)NPOP * ncell;
   bool coded = c->P.lq > 0;
@@ -518,12 +519,18 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
     codes = nullptr;
     coded = false;
   }
+  const size_t mom_step = (size_t)13 * ncell;
+  if (coded && cudaMalloc(&moms, (size_t)k * mom_step * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();  // not enough memory: the adjoint sums the moments itself
+    moms = nullptr;
+  }
   dvbm_status s = DVBM_OK;
   auto cleanup = [&]() {
     for (int i = 0; i < 2; ++i) if (lam[i]) c->pool.push_back(lam[i]);
     for (void* p : seg) c->pool.push_back(p);
     if (part) cudaFree(part);
     if (codes) cudaFree(codes);
+    if (moms) cudaFree(moms);
   };
   for (int i = 0; i < 2 && s == DVBM_OK; ++i) s = take_buffer(c, &lam[i]);
   for (int i = 0; i < k + (coded ? 1 : 0) && s == DVBM_OK; ++i) {
@@ -554,14 +561,16 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
     e = cudaMemcpyAsync(seg[0], c->ckpt[j], c->state_bytes_dev, cudaMemcpyDeviceToDevice, c->stream);
     const long long nrec = coded ? E - S : E - S - 1;
     for (long long t = 0; t < nrec && e == cudaSuccess; ++t) {
-      if (coded) e = launch_step_codes(seg[t], seg[t + 1], c->G, c->P, c->flag, codes + t * code_step, c->stream);
+      if (coded)
+        e = launch_step_codes(seg[t], seg[t + 1], c->G, c->P, c->flag, codes + t * code_step,
+                              moms ? moms + t * mom_step : nullptr, c->stream);
       else e = launch_step(0, seg[t], seg[t + 1], c->G, c->P, c->flag, c->stream);
       if (e == cudaSuccess && t + 1 < E - S) e = launch_ghost(0, seg[t + 1], c->G, c->P, c->M, c->bc, c->stream);
     }
     for (long long t = E - S - 1; t >= 0 && e == cudaSuccess; --t) {
       e = launch_adjoint_step((const double*)seg[t], (const double*)lam[a], (double*)lam[1 - a],
-                              part + slot * nblk * 4, coded ? codes + t * code_step : nullptr, c->G, c->P,
-                              c->stream);
+                              part + slot * nblk * 4, coded ? codes + t * code_step : nullptr,
+                              moms ? moms + t * mom_step : nullptr, c->G, c->P, c->stream);
       ++slot;
       a = 1 - a;
       if (e == cudaSuccess) e = launch_ghost(0, lam[a], c->G, c->P, c->M, per, c->stream);

@@ -19,8 +19,10 @@ cudaError_t launch_step(int storage, const void* src, void* dst, const Geom& G, 
                         unsigned int* flag, cudaStream_t st);
 // FP64 step with the rational limiter that also records the minmod branch
 // codes of every population's x and y slopes: codes[pop][y][x] = x | y << 2
+// moms (nullable): also store the 13 moments of each cell of the input state,
+// moms[k][y][x] in Moments field order
 cudaError_t launch_step_codes(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
-                              unsigned char* codes, cudaStream_t st);
+                              unsigned char* codes, double* moms, cudaStream_t st);
 cudaError_t launch_init(int storage, void* dst, const double* rho, const double* ux, const double* uy,
                         const double* T, const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
 cudaError_t launch_ghost(int storage, void* buf, const Geom& G, const Phys& P, const Macro& M,
@@ -53,7 +55,8 @@ int adjoint_blocks(const Geom& G);
 // codes: the branch codes recorded by launch_step_codes for this step, or
 // nullptr (the advection adjoint then derives the branches from X)
 cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial,
-                                const unsigned char* codes, const Geom& G, const Phys& P, cudaStream_t st);
+                                const unsigned char* codes, const double* moms, const Geom& G, const Phys& P,
+                                cudaStream_t st);
 cudaError_t launch_adjoint_final(const double* X, const double* rhob, const double* Tb, double* Lout, double* partial,
                                  const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
 cudaError_t launch_adjoint_init(const double* L, const double* rho, const double* ux, const double* uy,

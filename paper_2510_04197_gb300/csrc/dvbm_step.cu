@@ -186,7 +186,8 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
 template <class S, int PRC, bool RAT, bool CODES = false>
 __global__ void __launch_bounds__(256, 4) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
                                               unsigned int* __restrict__ flag,
-                                              unsigned char* __restrict__ codes = nullptr) {
+                                              unsigned char* __restrict__ codes = nullptr,
+                                              double* __restrict__ moms = nullptr) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   if (x >= G.Nx || y >= G.Ny) return;
@@ -211,6 +212,17 @@ __global__ void __launch_bounds__(256, 4) k_step(const S* __restrict__ src, S* _
     // sum w = 1, sum w xi^2 = 1 per axis, odd moments vanish
     m.m00 += P.fref0; m.m20 += P.fref0; m.m02 += P.fref0;
     m.g00 += P.gref0;
+  }
+  if constexpr (CODES) {
+    // the recomputing adjoint also keeps the cell's moments (13 planes of
+    // Nx * Ny doubles, Moments field order) for its collision part
+    if (moms) {
+      const long long cp = (long long)G.Nx * G.Ny, ci = (long long)y * G.Nx + x;
+      const double v[13] = {m.m00, m.m10, m.m01, m.m20, m.m11, m.m02, m.m30,
+                            m.m21, m.m12, m.m03, m.g00, m.g10, m.g01};
+#pragma unroll
+      for (int k = 0; k < 13; ++k) moms[k * cp + ci] = v[k];
+    }
   }
   Coeffs C = collision_coeffs<PRC>(m, P);
   if (C.bad) atomicOr(flag, 1u);
@@ -272,15 +284,15 @@ static cudaError_t launch_step_t(const void* src, void* dst, const Geom& G, cons
 }
 
 cudaError_t launch_step_codes(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
-                              unsigned char* codes, cudaStream_t st) {
+                              unsigned char* codes, double* moms, cudaStream_t st) {
   if (!(P.lq > 0) || !codes) return cudaErrorInvalidValue;
   dim3 block(32, 8);
   dim3 grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
   const double* s = (const double*)src;
   double* d = (double*)dst;
-  if (P.prc < 0) k_step<double, -1, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes);
-  else if (P.prc > 0) k_step<double, 1, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes);
-  else k_step<double, 0, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes);
+  if (P.prc < 0) k_step<double, -1, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes, moms);
+  else if (P.prc > 0) k_step<double, 1, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes, moms);
+  else k_step<double, 0, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes, moms);
   return cudaGetLastError();
 }
 

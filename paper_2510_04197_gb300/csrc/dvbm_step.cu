@@ -49,19 +49,21 @@ __constant__ long long c_khx[5][5] = {
     {khfix(4, 0), khfix(4, 1), khfix(4, 2), khfix(4, 3), khfix(4, 4)}};
 
 // This thread's fixed-point collision coefficients, kept in shared memory
-// (field k of thread t at [k * 256 + t]: consecutive threads, consecutive
+// (field k of thread t at [k * kCta + t]: consecutive threads, consecutive
 // words) rather than in 42 registers across the node loop, so that three
 // CTAs fit on an SM.  Field order as in CoeffsFix.
 constexpr int kFixFields = 21;
+constexpr int kTileY = 8;                 // CTA = 32 x kTileY cells
+constexpr int kCta = 32 * kTileY;
 struct FixView {
   const long long* b;
-  __device__ __forceinline__ long long operator()(int k) const { return b[k * 256]; }
+  __device__ __forceinline__ long long operator()(int k) const { return b[k * kCta]; }
 };
 __device__ __forceinline__ void fix_to_smem(const CoeffsFix& X, long long* b) {
   const long long v[kFixFields] = {X.f00, X.f10, X.f01, X.f20, X.f11, X.f02, X.f30, X.f21, X.f12, X.f03, X.f40,
                                    X.f31, X.f22, X.f13, X.f04, X.g00, X.g10, X.g01, X.g20, X.g11, X.g02};
 #pragma unroll
-  for (int k = 0; k < kFixFields; ++k) b[k * 256] = v[k];
+  for (int k = 0; k < kFixFields; ++k) b[k * kCta] = v[k];
 }
 // h^b of x-node p from the shared-memory coefficients (hfg_fix / hfg_fix_centre)
 __device__ __forceinline__ void hfg_fix_view(const FixView& X, long long k0, long long k1, long long k2, long long k3,
@@ -184,12 +186,12 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
 }
 
 template <class S, int PRC, bool RAT, bool CODES = false>
-__global__ void __launch_bounds__(256, 4) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
+__global__ void __launch_bounds__(kCta, 1024 / kCta) k_step(const S* __restrict__ src, S* __restrict__ dst, Geom G, Phys P,
                                               unsigned int* __restrict__ flag,
                                               unsigned char* __restrict__ codes = nullptr,
                                               double* __restrict__ moms = nullptr) {
   const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int y = blockIdx.y * kTileY + threadIdx.y;
   if (x >= G.Nx || y >= G.Ny) return;
   const long long off = cell_index(G, y, x);
   const S* s = src + off;
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(256, 4) k_step(const S* __restrict__ src, S* _
   // bracket (equilibrium evaluation minus the relaxed reference) at
   // FP64-or-better precision, rounded to float only in the update
   const float a1f = (float)C.a1;
-  __shared__ long long s_fix[kFixFields * 256];
+  __shared__ long long s_fix[kFixFields * kCta];
   const int tid = threadIdx.y * 32 + threadIdx.x;
   int Ef, Eg;
   {
@@ -264,8 +266,8 @@ __global__ void __launch_bounds__(256, 4) k_step(const S* __restrict__ src, S* _
 template <class S>
 static cudaError_t launch_step_t(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
                                  cudaStream_t st) {
-  dim3 block(32, 8);
-  dim3 grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
+  dim3 block(32, kTileY);
+  dim3 grid((G.Nx + 31) / 32, (G.Ny + kTileY - 1) / kTileY);
   const S* s = (const S*)src;
   S* d = (S*)dst;
   // the rational limiter form matters only for FP64 storage
@@ -286,8 +288,8 @@ static cudaError_t launch_step_t(const void* src, void* dst, const Geom& G, cons
 cudaError_t launch_step_codes(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
                               unsigned char* codes, double* moms, cudaStream_t st) {
   if (!(P.lq > 0) || !codes) return cudaErrorInvalidValue;
-  dim3 block(32, 8);
-  dim3 grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
+  dim3 block(32, kTileY);
+  dim3 grid((G.Nx + 31) / 32, (G.Ny + kTileY - 1) / kTileY);
   const double* s = (const double*)src;
   double* d = (double*)dst;
   if (P.prc < 0) k_step<double, -1, true, true><<<grid, block, 0, st>>>(s, d, G, P, flag, codes, moms);

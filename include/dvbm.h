@@ -110,8 +110,10 @@ dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, double Pr, 
 /* Equilibrium initial conditions (Sec. III.A.3): populations = f^eq, g^eq of
  * the given rho, u_x, u_y, T at the cell centres; fills ghost layers; fixes
  * dt = cfl min(dx, dy) / max(|u| + sqrt(gamma R T)) over these fields unless
- * opts.dt > 0.  Resets the step counter.  Errors: EINVAL (null pointer,
- * rho <= 0 or T <= 0 or non-finite input: DVBM_EINVAL), ECUDA. */
+ * opts.dt > 0.  Resets the step counter.  Host fields (on_device = 0) pass
+ * through a staging buffer of 4 Nx Ny doubles that the context allocates on
+ * first use and keeps until dvbm_destroy.  Errors: EINVAL (null pointer,
+ * rho <= 0 or T <= 0 or non-finite input: DVBM_EINVAL), ENOMEM, ECUDA. */
 dvbm_status dvbm_init(dvbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
                       const double* T, int on_device);
 
@@ -121,7 +123,9 @@ dvbm_status dvbm_init(dvbm_ctx* ctx, const double* rho, const double* ux, const 
 dvbm_status dvbm_step(dvbm_ctx* ctx, int n);
 
 /* rho, u_x, u_y, T of the current state (Sec. II.D.1 moments, T from
- * Eq. Total_energy_MB).  Any output pointer may be NULL to skip it. */
+ * Eq. Total_energy_MB).  Any output pointer may be NULL to skip it.  Host
+ * outputs (on_device = 0) go through the context's staging buffer (see
+ * dvbm_init); the call returns once they are written. */
 dvbm_status dvbm_moments(dvbm_ctx* ctx, double* rho, double* ux, double* uy, double* T,
                          int on_device);
 

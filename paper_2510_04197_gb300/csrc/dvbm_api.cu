@@ -44,6 +44,7 @@ struct dvbm_ctx {
   std::vector<void*> ckpt;             // ckpt[j] = state at step j * record_every
   std::vector<void*> pool;             // spare state buffers
   double* init_fields = nullptr;       // rho, ux, uy, T of the recorded dvbm_init
+  double* stage = nullptr;             // 4 Nx Ny doubles staging host fields (allocated on first use)
   size_t state_bytes_dev = 0;
 };
 
@@ -285,10 +286,11 @@ static dvbm_status stage_fields(dvbm_ctx* c, DevFields& F, const double* const i
     for (int k = 0; k < 4; ++k) F.p[k] = in[k];
     return DVBM_OK;
   }
-  CUDA_TRY(c, cudaMalloc(&F.owned, 4 * n * sizeof(double)));
+  // one staging buffer per context, reused (stream-ordered) by every host transfer
+  if (!c->stage) CUDA_TRY(c, cudaMalloc(&c->stage, 4 * n * sizeof(double)));
   for (int k = 0; k < 4; ++k) {
-    CUDA_TRY(c, cudaMemcpyAsync(F.owned + k * n, in[k], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    F.p[k] = F.owned + k * n;
+    CUDA_TRY(c, cudaMemcpyAsync(c->stage + k * n, in[k], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    F.p[k] = c->stage + k * n;
   }
   return DVBM_OK;
 }
@@ -409,14 +411,12 @@ extern "C" dvbm_status dvbm_moments(dvbm_ctx* c, double* rho, double* ux, double
     CUDA_TRY(c, l_moments(c, c->buf[c->cur], rho, ux, uy, T));
     return DVBM_OK;
   }
-  double* tmp = nullptr;
-  CUDA_TRY(c, cudaMalloc(&tmp, 4 * n * sizeof(double)));
+  if (!c->stage) CUDA_TRY(c, cudaMalloc(&c->stage, 4 * n * sizeof(double)));
+  double* tmp = c->stage;
   cudaError_t e = l_moments(c, c->buf[c->cur], tmp, tmp + n, tmp + 2 * n, tmp + 3 * n);
   for (int k = 0; k < 4 && e == cudaSuccess; ++k)
     if (outs[k]) e = cudaMemcpyAsync(outs[k], tmp + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  dvbm_status s = e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "moments: %s", cudaGetErrorString(e));
-  cudaFree(tmp);
-  return s;
+  return e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "moments: %s", cudaGetErrorString(e));
 }
 
 extern "C" dvbm_status dvbm_totals(dvbm_ctx* c, double out[4]) {
@@ -620,5 +620,6 @@ extern "C" void dvbm_destroy(dvbm_ctx* c) {
   for (void* p : c->ckpt) cudaFree(p);
   for (void* p : c->pool) cudaFree(p);
   if (c->init_fields) cudaFree(c->init_fields);
+  if (c->stage) cudaFree(c->stage);
   delete c;
 }

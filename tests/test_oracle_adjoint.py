@@ -56,3 +56,34 @@ def test_oracle_adjoint_matches_finite_differences(Pr):
         fd = (loss_and_grad(F, *ap, dt, n, Tg.rho, Tg.T, False)[0]
               - loss_and_grad(F, *am, dt, n, Tg.rho, Tg.T, False)[0]) / (2 * hp)
         assert abs(fd - g[4 + i]) < 1e-6 * abs(g[4 + i]), (name, fd, g[4 + i])
+
+
+def test_oracle_adjoint_dot_product_against_forward_mode():
+    """Dot-product test of the discrete adjoint: for the map (rho0, u0, T0) ->
+    (rho_n, T_n) of the oracle, the forward-mode directional derivative J v
+    (torch.func.jvp, dual numbers) and the reverse-mode product J^T w
+    (torch.autograd) satisfy <w, J v> = <J^T w, v> to roundoff."""
+    F = I.random_smooth(8, 6, seed=11, amp=0.08, Ma=0.4)
+    gamma, mu, dt, n, Pr = 1.4, 2e-3, 2e-4, 3, 0.71
+    lat = O.Lattice()
+    Ny, Nx = F.rho.shape
+    grid = O.Grid(Nx, Ny, F.Lx, F.Ly)
+    P = O.Params(Pr=Pr, gamma=gamma, mu=mu)
+
+    def forward(rho, ux, uy, T):
+        f, g = O.init_populations(lat, P, rho, ux, uy, T)
+        for _ in range(n):
+            f, g = O.step(lat, P, grid, f, g, dt)
+        r, _, _, t, _ = O.macroscopic(lat, P, f, g)
+        return torch.stack([r, t])
+
+    x = tuple(torch.tensor(getattr(F, k), dtype=DT) for k in ("rho", "ux", "uy", "T"))
+    rng = np.random.default_rng(3)
+    v = tuple(torch.tensor(rng.standard_normal(F.rho.shape), dtype=DT) for _ in range(4))
+    w = torch.tensor(rng.standard_normal((2,) + F.rho.shape), dtype=DT)
+    _, Jv = torch.func.jvp(forward, x, v)
+    xr = tuple(a.clone().requires_grad_(True) for a in x)
+    JTw = torch.autograd.grad(forward(*xr), xr, grad_outputs=w)
+    lhs = float((w * Jv).sum())
+    rhs = float(sum((a * b).sum() for a, b in zip(JTw, v)))
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0), (lhs, rhs)

@@ -177,3 +177,55 @@ def test_acoustic_dissipation_matches_linearised_nsf(D, split, lattice, Pr, gamm
     nuL_model = (2 - 2 / 2) * nu + zeta
     nuL = so.least_squares(resid, [nuL_model]).x[0]
     assert abs(nuL / nuL_model - 1) < 0.05, (nuL, nuL_model)
+
+
+def test_config1_decay_rates_match_closed_forms(D):
+    """64 x 64 shear + entropy waves over a Ma = 0.1 mean flow (Pr 0.71,
+    gamma 1.4, mu 0.01, CFL 0.01, 1000 steps): the shear wave decays at
+    nu k^2 (nu = mu / rho) and the entropy mode follows the linearised NSF
+    system with alpha = nu / Pr (Sec. III.D.1, III.D.3), fitted from the
+    CUDA path's fields, within 2 % (shear) and 3 % (thermal)."""
+    gamma, Pr, mu, N = 1.4, 0.71, 0.01, 64
+    F = I.wave_decay(N, N, Ma=0.1, amp=1e-3)
+    u0 = 0.1 * math.sqrt(gamma)
+    sim = D.Simulation(N, N, Pr, gamma, mu, cfl=0.01, check_every=-1)
+    sim.init(*(torch.tensor(a) for a in (F.rho, F.ux, F.uy, F.T)))
+    x = (np.arange(N) + 0.5) / N
+    ex = np.exp(-2j * np.pi * x)[None, :]
+    ey = np.exp(-2j * np.pi * x)[:, None]  # the same cell centres along y
+    k = 2 * np.pi
+    dt = sim.dt
+
+    def amps():
+        m = {kk: v.cpu().numpy() for kk, v in sim.moments().items()}
+        t = sim.steps * dt
+        shear = (m["uy"] * ex).mean() * np.exp(2j * np.pi * u0 * t)  # undo the mean-flow advection
+        # the entropy mode varies along y: (rho, longitudinal velocity u_y, T) amplitudes
+        # (the shear wave's u_y depends on x only and does not project onto e^{-2 pi i y})
+        ent = np.array([(m["rho"] * ey).mean(), (m["uy"] * ey).mean(), (m["T"] * ey).mean()])
+        return t, shear, ent
+
+    sim.step(200)  # past the non-hydrodynamic transient
+    t1, s1, e1 = amps()
+    hist = []
+    for _ in range(4):
+        sim.step(200)
+        hist.append(amps())
+    sim.close()
+    t_end, s_end, _ = hist[-1]
+    nu_fit = -math.log(abs(s_end) / abs(s1)) / (k * k * (t_end - t1))
+    assert abs(nu_fit / mu - 1) < 0.02, nu_fit
+    R, Cv = 1.0, 1.0 / (gamma - 1)
+    nuL = mu + (1 - R / Cv) * mu
+
+    def resid(q):
+        M = np.array([[0, -1j * k, 0], [-1j * k * R, -nuL * k * k, -1j * k * R],
+                      [0, -1j * k * R / Cv, -gamma * q[0] * k * k]])
+        out = []
+        for tt, _, c in hist:
+            d = (sl.expm(M * (tt - t1)) @ e1 - c) / abs(e1[0])
+            out += [d.real, d.imag]
+        return np.concatenate(out)
+
+    alpha = so.least_squares(resid, [mu / Pr]).x[0]
+    assert abs(alpha / (mu / Pr) - 1) < 0.03, alpha

@@ -103,3 +103,31 @@ def test_checkpoint_resume_is_bitwise(D):
     assert c.steps == 10
     c.step(10)
     assert torch.equal(c.populations(), ref)
+
+
+@pytest.mark.parametrize("beta", [1.0, 1.5, 2.0, math.sqrt(2.0)])
+def test_limiter_parameter_range(D, beta):
+    """The generalized limiter over its range (Sec. III.A.2: beta = 1 is
+    minmod, beta = 2 the MC limiter).  Rational beta run the small-integer
+    limiter, irrational beta (sqrt 2) the 64-bit fixed-point one; O(1)
+    gradients on a ragged grid, 100 steps, fields within 1e-12."""
+    F = I.random_smooth(40, 24, seed=5, amp=0.15, Ma=0.6)
+    sim, g = gpu_run(D, F, 0.71, 1.4, 2e-3, 100, dt=2e-4, beta=beta)
+    _, o = oracle_run(F, 0.71, 1.4, 2e-3, sim.dt, 100, beta=beta)
+    e = field_errors(g, o)
+    assert max(e.values()) < 1e-12, (beta, e)
+
+
+@pytest.mark.parametrize("R,T_ref", [(0.5, 2.0), (287.0, 300.0)])
+def test_gas_constant_and_reference_temperature(D, R, T_ref):
+    """Lattice velocities scale with c = sqrt(R T_ref) (App. G): the same
+    dimensionless flow in physical units (u c, T T_ref, mu c) stays within
+    1e-12 of the oracle for air-like R and T_ref too."""
+    F0 = I.random_smooth(40, 24, seed=7, amp=0.1, Ma=0.5)
+    c = math.sqrt(R * T_ref)
+    F = I.Fields(F0.rho, F0.ux * c, F0.uy * c, F0.T * T_ref, F0.Lx, F0.Ly)
+    mu = 2e-3 * c
+    sim, g = gpu_run(D, F, 0.71, 1.4, mu, 100, dt=2e-4 / c, R=R, T_ref=T_ref)
+    _, o = oracle_run(F, 0.71, 1.4, mu, sim.dt, 100, R=R, T_ref=T_ref)
+    e = field_errors(g, o)
+    assert max(e.values()) < 1e-12, (R, T_ref, e)

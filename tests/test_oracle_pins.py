@@ -411,3 +411,22 @@ def test_step_patch_matches_full_step():
     for k, (y, x) in enumerate(cells):
         assert torch.allclose(fn[:, k], f1[:, y, x], atol=1e-15, rtol=1e-14)
         assert torch.allclose(gn[:, k], g1[:, y, x], atol=1e-15, rtol=1e-14)
+
+
+def test_similarity_under_gas_constant_and_reference_temperature():
+    """Dimensional analysis: with velocities scaled by c = sqrt(R T_ref),
+    temperatures by T_ref, mu by c and dt by 1/c, the lattice (App. G,
+    v_i = c xi_i) and every relaxation rate scale consistently, so the density
+    field is the same function of the dimensionless inputs, and u / c, T / T_ref
+    too; a wrong power of c or T_ref anywhere breaks it."""
+    from helpers import oracle_run
+    from paper_2510_04197_gb300 import inputs as I
+    F0 = I.random_smooth(20, 12, seed=7, amp=0.1, Ma=0.5)
+    out = {}
+    for R, T_ref in ((1.0, 1.0), (287.0, 300.0)):
+        c = math.sqrt(R * T_ref)
+        F = I.Fields(F0.rho, F0.ux * c, F0.uy * c, F0.T * T_ref, F0.Lx, F0.Ly)
+        _, o = oracle_run(F, 0.71, 1.4, 2e-3 * c, 2e-4 / c, 30, R=R, T_ref=T_ref)
+        out[(R, T_ref)] = (o["rho"], o["ux"] / c, o["T"] / T_ref)
+    for a, b in zip(out[(1.0, 1.0)], out[(287.0, 300.0)]):
+        assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()

@@ -131,3 +131,31 @@ def test_gas_constant_and_reference_temperature(D, R, T_ref):
     _, o = oracle_run(F, 0.71, 1.4, mu, sim.dt, 100, R=R, T_ref=T_ref)
     e = field_errors(g, o)
     assert max(e.values()) < 1e-12, (R, T_ref, e)
+
+
+@pytest.mark.parametrize("Pr", [1.0, 2.0])
+def test_fp32_deviation_storage_other_prandtl_branches(D, Pr):
+    """FP32-deviation storage in the Pr = 1 and Pr > 1 branches of Table I
+    (smooth O(0.1) flow on a ragged grid, 300 steps): relative L-inf error
+    against the FP64 oracle at most 1e-5."""
+    F = I.random_smooth(40, 24, seed=3, amp=0.05, Ma=0.3)
+    sim, g = gpu_run(D, F, Pr, 1.4, 2e-3, 300, storage=1, dt=2e-4)
+    _, o = oracle_run(F, Pr, 1.4, 2e-3, sim.dt, 300)
+    e = field_errors(g, o)
+    assert max(e.values()) < 1e-5, (Pr, e)
+
+
+def test_fp32_deviation_storage_with_walls(D):
+    """FP32-deviation storage with the no-slip isothermal walls (ghost node +
+    non-equilibrium extrapolation, Sec. III.E): thermal Couette start-up,
+    4 x 24 cells, 200 steps, relative L-inf error against the FP64 oracle
+    at most 1e-5."""
+    cs = I.couette(Nx=4, Ny=24, Ma=0.5, gamma=1.4)
+    F = cs.fields
+    dt = min(0.4 * (F.Ly / 24) / math.sqrt(5 + math.sqrt(10)), 0.25 * cs.mu / 2.0)
+    bcs = [D.PERIODIC, D.PERIODIC, (D.WALL, (0.0, 0.0), cs.T_C), (D.WALL, (cs.u0, 0.0), cs.T_H)]
+    sim, g = gpu_run(D, F, 2.0, 1.4, cs.mu, 200, storage=1, bcs=bcs, dt=dt)
+    ob = (O.BC(), O.BC(), O.BC(O.WALL, (0.0, 0.0), cs.T_C), O.BC(O.WALL, (cs.u0, 0.0), cs.T_H))
+    _, o = oracle_run(F, 2.0, 1.4, cs.mu, dt, 200, bcs=ob)
+    e = field_errors(g, o)
+    assert max(e.values()) < 1e-5, e

@@ -309,51 +309,15 @@ __device__ __forceinline__ void expand_q3(const double (&h)[3], double (&t)[5]) 
 // ---- limited slope of the NND reconstruction (Sec. III.A.2) --------------
 // sigma(a, b) = (b/2) phi(a/b) = 1/2 minmod3(beta a, (a+b)/2, beta b)
 //             = minmod3(hb a, (a+b)/4, hb b),  hb = beta/2,
-// (division-free; 0 if a and b differ in sign; b = 0 gives 0).
-// When a and b share a sign, the three candidates x = hb a, y = (a+b)/4,
-// z = hb b share it too, and for doubles of one sign the signed-int64 order of
-// the raw bit patterns is the order of magnitudes (sign-magnitude encoding).
-// So the minimum-magnitude candidate, sign included, is the signed-int64
-// minimum of the bit patterns: no FP64 compare, abs or min is needed.
-__device__ __forceinline__ double minmod_sel(double a, double b, double x, double y, double z) {
-  const long long bx = __double_as_longlong(x), by = __double_as_longlong(y), bz = __double_as_longlong(z);
-  long long mn = bx < by ? bx : by;
-  mn = mn < bz ? mn : bz;
-  const int same = (__double2hiint(a) ^ __double2hiint(b)) >= 0;
-  return __longlong_as_double(same ? mn : 0ll);
-}
-__device__ __forceinline__ double limited_slope(double a, double b, double hb) {
-  return minmod_sel(a, b, hb * a, 0.25 * (a + b), hb * b);
-}
+// (division-free; 0 if a and b differ in sign; b = 0 gives 0).  This float
+// form serves the FP32-deviation storage; FP64 storage runs the same limiter
+// exactly on integers (below).
 __device__ __forceinline__ float limited_slope(float a, float b, float hb) {
   const float x = hb * a, z = hb * b, y = 0.25f * (a + b);
   const float mn = fminf(fminf(fabsf(x), fabsf(y)), fabsf(z));
   return ((__float_as_int(a) ^ __float_as_int(b)) >= 0) ? copysignf(mn, a) : 0.0f;
 }
 
-// Flux difference F_{j+1/2} - F_{j-1/2} of the upwind-limited face values
-// along a stride; SGN = sign of the velocity component (never 0 here).
-//   v > 0: faces f_{j-1} + sigma_{j-1}, f_j + sigma_j
-//   v < 0: faces f_j - sigma_j, f_{j+1} - sigma_{j+1}
-// The candidate hb * D of the difference shared by the two slopes is formed once.
-__device__ __forceinline__ double flux_difference_d(const double* __restrict__ ptr, long long stride, double hb,
-                                                    int sgn) {
-  if (sgn > 0) {
-    const double fm2 = __ldg(ptr - 2 * stride), fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride);
-    const double Dm = fm1 - fm2, D0 = f0 - fm1, Dp = fp1 - f0;
-    const double rm = hb * Dm, r0 = hb * D0, rp = hb * Dp;
-    const double s0 = minmod_sel(D0, Dp, r0, 0.25 * (D0 + Dp), rp);
-    const double sm = minmod_sel(Dm, D0, rm, 0.25 * (Dm + D0), r0);
-    return D0 + s0 - sm;
-  } else {
-    const double fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride), fp2 = __ldg(ptr + 2 * stride);
-    const double D0 = f0 - fm1, Dp = fp1 - f0, Dpp = fp2 - fp1;
-    const double r0 = hb * D0, rp = hb * Dp, rpp = hb * Dpp;
-    const double sp = minmod_sel(Dp, Dpp, rp, 0.25 * (Dp + Dpp), rpp);
-    const double s0 = minmod_sel(D0, Dp, r0, 0.25 * (D0 + Dp), rp);
-    return Dp - sp + s0;
-  }
-}
 // ---- FP64 advection in block floating point on the integer pipe ----------
 // GB300 runs FP64 at 1/64 of the FP32 rate, while integer ops are cheap.  The
 // four values of one upwind stencil are brought to their largest exponent E
@@ -450,31 +414,6 @@ __device__ __forceinline__ CoeffsFix coeffs_to_fix(const Coeffs& C) {
 }
 
 __device__ __forceinline__ long long mhk(long long x, long long k) { return __mul64hi(x, k); }
-
-// h^b of x-node p (value = h 2^(E - 1081 - kd(p))); k0..k4 = khfix(p, 0..4)
-__device__ __forceinline__ void hfg_fix(const CoeffsFix& X, long long k0, long long k1, long long k2, long long k3,
-                                        long long k4, long long (&hf)[5], long long (&hg)[3]) {
-  hf[0] = mhk(X.f00, k0) + mhk(X.f10, k1) + mhk(X.f20, k2) + mhk(X.f30, k3) + mhk(X.f40, k4);
-  hf[1] = mhk(X.f01, k0) + mhk(X.f11, k1) + mhk(X.f21, k2) + mhk(X.f31, k3);
-  hf[2] = mhk(X.f02, k0) + mhk(X.f12, k1) + mhk(X.f22, k2);
-  hf[3] = mhk(X.f03, k0) + mhk(X.f13, k1);
-  hf[4] = mhk(X.f04, k0);
-  hg[0] = mhk(X.g00, k0) + mhk(X.g10, k1) + mhk(X.g20, k2);
-  hg[1] = mhk(X.g01, k0) + mhk(X.g11, k1);
-  hg[2] = mhk(X.g02, k0);
-}
-// centre node (xi = 0: He_1 = He_3 = 0)
-__device__ __forceinline__ void hfg_fix_centre(const CoeffsFix& X, long long (&hf)[5], long long (&hg)[3]) {
-  constexpr long long k0 = khfix(0, 0), k2 = khfix(0, 2), k4 = khfix(0, 4);
-  hf[0] = mhk(X.f00, k0) + mhk(X.f20, k2) + mhk(X.f40, k4);
-  hf[1] = mhk(X.f01, k0) + mhk(X.f21, k2);
-  hf[2] = mhk(X.f02, k0) + mhk(X.f22, k2);
-  hf[3] = mhk(X.f03, k0);
-  hf[4] = mhk(X.f04, k0);
-  hg[0] = mhk(X.g00, k0) + mhk(X.g20, k2);
-  hg[1] = mhk(X.g01, k0);
-  hg[2] = mhk(X.g02, k0);
-}
 
 // shift the N values so that the largest magnitude has its top bit at 2^60;
 // returns the shift (value of h after the call = h 2^(-sh) of its old scale)
@@ -649,20 +588,22 @@ __device__ __forceinline__ double flux_difference_rat_code(const double* __restr
   return ll_to_double_scaled(F, E - 1074);
 }
 
+// Flux difference F_{j+1/2} - F_{j-1/2} of the upwind-limited face values
+// along a stride (float, FP32-deviation storage); SGN = sign of the velocity
+// component (never 0 here).
+//   v > 0: faces f_{j-1} + sigma_{j-1}, f_j + sigma_j
+//   v < 0: faces f_j - sigma_j, f_{j+1} - sigma_{j+1}
 template <int SGN, class T>
 __device__ __forceinline__ T flux_difference(const T* __restrict__ ptr, long long stride, T hb) {
-  if constexpr (sizeof(T) == 8) {
-    return flux_difference_d(ptr, stride, hb, SGN);
+  static_assert(sizeof(T) == 4, "FP64 storage uses the integer flux differences");
+  if (SGN > 0) {
+    const T fm2 = __ldg(ptr - 2 * stride), fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride);
+    const T Dm = fm1 - fm2, D0 = f0 - fm1, Dp = fp1 - f0;
+    return D0 + limited_slope(D0, Dp, hb) - limited_slope(Dm, D0, hb);
   } else {
-    if (SGN > 0) {
-      const T fm2 = __ldg(ptr - 2 * stride), fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride);
-      const T Dm = fm1 - fm2, D0 = f0 - fm1, Dp = fp1 - f0;
-      return D0 + limited_slope(D0, Dp, hb) - limited_slope(Dm, D0, hb);
-    } else {
-      const T fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride), fp2 = __ldg(ptr + 2 * stride);
-      const T D0 = f0 - fm1, Dp = fp1 - f0, Dpp = fp2 - fp1;
-      return Dp - limited_slope(Dp, Dpp, hb) + limited_slope(D0, Dp, hb);
-    }
+    const T fm1 = __ldg(ptr - stride), f0 = __ldg(ptr), fp1 = __ldg(ptr + stride), fp2 = __ldg(ptr + 2 * stride);
+    const T D0 = f0 - fm1, Dp = fp1 - f0, Dpp = fp2 - fp1;
+    return Dp - limited_slope(Dp, Dpp, hb) + limited_slope(D0, Dp, hb);
   }
 }
 

@@ -65,7 +65,7 @@ __device__ __forceinline__ void fix_to_smem(const CoeffsFix& X, long long* b) {
 #pragma unroll
   for (int k = 0; k < kFixFields; ++k) b[k * kCta] = v[k];
 }
-// h^b of x-node p from the shared-memory coefficients (hfg_fix / hfg_fix_centre)
+// h^b of x-node p from the shared-memory coefficients (value = h 2^(E - 1081 - kd(p)))
 __device__ __forceinline__ void hfg_fix_view(const FixView& X, long long k0, long long k1, long long k2, long long k3,
                                              long long k4, long long (&hf)[5], long long (&hg)[3]) {
   hf[0] = mhk(X(0), k0) + mhk(X(1), k1) + mhk(X(3), k2) + mhk(X(6), k3) + mhk(X(10), k4);

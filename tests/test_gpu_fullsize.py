@@ -74,3 +74,28 @@ def test_fullsize_step_matches_oracle_at_sampled_cells(D, storage):
     ef = (fg - fo).abs().max() / fo.abs().max()
     eg = (gg - go).abs().max() / go.abs().max()
     assert ef < tol and eg < tol, (float(ef), float(eg))
+
+
+def test_fullsize_d2q16_step_matches_oracle_at_sampled_cells(D):
+    """The same check for the total-energy split (I) on D2Q16, the bench's
+    third leg: one CUDA step at 4096^2 against the oracle's update of sampled
+    cells, every population within 1e-13 of the largest."""
+    F = I.multimode(N, seed=0, rms_Ma=0.3)
+    sim = D.Simulation(N, N, 0.71, 1.4, 5e-5, lattice=D.D2Q16_SPLIT_I, check_every=-1)
+    sim.init(*(torch.tensor(a) for a in (F.rho, F.ux, F.uy, F.T)))
+    sim.step(3)
+    cells = sample_cells()
+    before = patches(sim.populations(), cells)  # [32, B, 5, 5]
+    sim.step(1)
+    after = sim.populations()
+    ys = torch.tensor([c[0] for c in cells], device=after.device)
+    xs = torch.tensor([c[1] for c in cells], device=after.device)
+    got = after[:, ys, xs].double().cpu()
+    lat = O.Lattice(kind="D2Q16")
+    perm = abi_to_oracle_perm(lat)
+    P = O.Params(Pr=0.71, gamma=1.4, mu=5e-5, split="I")
+    fo, go = O.step_patch(lat, P, O.Grid(N, N), before[:16][perm], before[16:][perm], sim.dt)
+    fg, gg = got[:16][perm], got[16:][perm]
+    ef = (fg - fo).abs().max() / fo.abs().max()
+    eg = (gg - go).abs().max() / go.abs().max()
+    assert ef < 1e-13 and eg < 1e-13, (float(ef), float(eg))

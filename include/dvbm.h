@@ -43,7 +43,9 @@ typedef enum {
   DVBM_ENOMEM = 2,    /* device allocation failed */
   DVBM_ECUDA = 3,     /* a CUDA runtime call failed */
   DVBM_EUNSTABLE = 4, /* a cell reached rho <= 0, T <= 0 or a non-finite value */
-  DVBM_ETIMEOUT = 5,  /* the stream did not finish within opts.timeout_s */
+  DVBM_ETIMEOUT = 5,  /* the stream did not finish within opts.timeout_s; the
+                         work queued on it stays queued and runs on, and a
+                         later call waits for it again (see timeout_s) */
   DVBM_ESTATE = 6     /* call not valid in the context's current state */
 } dvbm_status;
 
@@ -90,7 +92,17 @@ typedef struct {
   int check_every;   /* dvbm_step checks the instability flag every k steps
                         (default 0: once at the end of each dvbm_step call;
                         < 0: never) */
-  double timeout_s;  /* host wait limit for a check (default 600 s) */
+  double timeout_s;  /* limit, in seconds, on every host wait for the stream
+                        (default 600 s; <= 0 selects the default): the
+                        instability checks, dvbm_init, dvbm_moments and
+                        dvbm_totals with host outputs, dvbm_get_state /
+                        dvbm_set_state, dvbm_adjoint.  The stream is drained
+                        under this limit before any copy into or out of
+                        pageable host memory (such a copy would otherwise
+                        block the calling thread without a limit).  A device
+                        temporary that queued work may still use after an
+                        ETIMEOUT is freed by dvbm_destroy, which synchronises
+                        the stream first. */
 } dvbm_opts;
 
 /* Fill *opts with the defaults listed above (Lx = 1, Ly = 0 meaning
@@ -144,7 +156,9 @@ dvbm_status dvbm_totals(dvbm_ctx* ctx, double out[4]);
 size_t dvbm_state_bytes(const dvbm_ctx* ctx);
 
 /* Copy the current state out / in (checkpoint / resume).  bytes must equal
- * dvbm_state_bytes.  set_state refills the ghost layers. */
+ * dvbm_state_bytes.  set_state refills the ghost layers and clears the
+ * instability flag (a run that returned EUNSTABLE resumes from a restored
+ * state); the restored state is checked by the next step like any other. */
 dvbm_status dvbm_get_state(dvbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 dvbm_status dvbm_set_state(dvbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
 

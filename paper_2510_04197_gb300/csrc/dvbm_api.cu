@@ -45,6 +45,7 @@ struct dvbm_ctx {
   std::vector<void*> pool;             // spare state buffers
   double* init_fields = nullptr;       // rho, ux, uy, T of the recorded dvbm_init
   double* stage = nullptr;             // 4 Nx Ny doubles staging host fields (allocated on first use)
+  std::vector<void*> in_flight;        // temporaries of calls that timed out, freed by dvbm_destroy
   size_t state_bytes_dev = 0;
 };
 
@@ -229,17 +230,35 @@ static dvbm_status wait_stream(dvbm_ctx* c) {
     if (e == cudaSuccess) break;
     if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return fail(c, DVBM_ECUDA, "stream error: %s", cudaGetErrorString(e)); }
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (el > c->opts.timeout_s) { cudaEventDestroy(ev); return fail(c, DVBM_ETIMEOUT, "stream did not finish within %.1f s", c->opts.timeout_s); }
+    if (el > c->opts.timeout_s) { cudaEventDestroy(ev); return fail(c, DVBM_ETIMEOUT, "stream did not finish within %g s", c->opts.timeout_s); }
     if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
   cudaEventDestroy(ev);
   return DVBM_OK;
 }
 
+// Device -> host copy under the time limit. A copy into pageable host memory returns only once
+// it has completed, i.e. once the stream has run everything queued before it, so a hung or slow
+// stream would block inside the copy, past timeout_s. The queued work is therefore waited for
+// first, under the limit; the copy then finds the stream idle.
+static dvbm_status drain_then_copy(dvbm_ctx* c, void* dst, const void* src, size_t bytes) {
+  dvbm_status s = wait_stream(c);
+  if (s != DVBM_OK) return s;
+  const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return fail(c, DVBM_ECUDA, "device to host copy: %s", cudaGetErrorString(e));
+  return wait_stream(c);
+}
+
+// A temporary that queued work may still use after a timeout is not freed here (cudaFree would
+// wait for that work, past the limit): dvbm_destroy frees it after synchronising the stream.
+static void release_temporary(dvbm_ctx* c, void* p, dvbm_status s) {
+  if (s == DVBM_ETIMEOUT) c->in_flight.push_back(p);
+  else cudaFree(p);
+}
+
 static dvbm_status check_flag(dvbm_ctx* c) {
   unsigned int h = 0;
-  CUDA_TRY(c, cudaMemcpyAsync(&h, c->flag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
-  dvbm_status s = wait_stream(c);
+  dvbm_status s = drain_then_copy(c, &h, c->flag, sizeof h);
   if (s != DVBM_OK) return s;
   if (h) return fail(c, DVBM_EUNSTABLE, "a cell reached rho <= 0, T <= 0 or a non-finite value (after %lld steps)", c->steps);
   return DVBM_OK;
@@ -288,6 +307,9 @@ static dvbm_status stage_fields(dvbm_ctx* c, DevFields& F, const double* const i
   }
   // one staging buffer per context, reused (stream-ordered) by every host transfer
   if (!c->stage) CUDA_TRY(c, cudaMalloc(&c->stage, 4 * n * sizeof(double)));
+  // a copy from pageable host memory may wait for the stream: drain it first, under the limit
+  dvbm_status s = wait_stream(c);
+  if (s != DVBM_OK) return s;
   for (int k = 0; k < 4; ++k) {
     CUDA_TRY(c, cudaMemcpyAsync(c->stage + k * n, in[k], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     F.p[k] = c->stage + k * n;
@@ -344,8 +366,7 @@ extern "C" dvbm_status dvbm_init(dvbm_ctx* c, const double* rho, const double* u
   const long long n = (long long)c->Nx * c->Ny;
   CUDA_TRY(c, launch_speed(F.p[0], F.p[1], F.p[2], F.p[3], n, c->partial, c->nred, c->M, c->stream));
   std::vector<double> h(2 * c->nred);
-  CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  s = wait_stream(c);
+  s = drain_then_copy(c, h.data(), c->partial, h.size() * sizeof(double));
   if (s != DVBM_OK) return s;
   double vmax = 0.0, bad = 0.0;
   for (int b = 0; b < c->nred; ++b) { vmax = std::fmax(vmax, h[2 * b]); bad += h[2 * b + 1]; }
@@ -413,10 +434,13 @@ extern "C" dvbm_status dvbm_moments(dvbm_ctx* c, double* rho, double* ux, double
   }
   if (!c->stage) CUDA_TRY(c, cudaMalloc(&c->stage, 4 * n * sizeof(double)));
   double* tmp = c->stage;
-  cudaError_t e = l_moments(c, c->buf[c->cur], tmp, tmp + n, tmp + 2 * n, tmp + 3 * n);
-  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-    if (outs[k]) e = cudaMemcpyAsync(outs[k], tmp + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  return e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "moments: %s", cudaGetErrorString(e));
+  CUDA_TRY(c, l_moments(c, c->buf[c->cur], tmp, tmp + n, tmp + 2 * n, tmp + 3 * n));
+  // drained first, under the limit: a copy into pageable memory would otherwise wait unbounded
+  dvbm_status s = wait_stream(c);
+  if (s != DVBM_OK) return s;
+  for (int k = 0; k < 4; ++k)
+    if (outs[k]) CUDA_TRY(c, cudaMemcpyAsync(outs[k], tmp + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return wait_stream(c);
 }
 
 extern "C" dvbm_status dvbm_totals(dvbm_ctx* c, double out[4]) {
@@ -424,8 +448,7 @@ extern "C" dvbm_status dvbm_totals(dvbm_ctx* c, double out[4]) {
   if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
   CUDA_TRY(c, l_totals(c, c->buf[c->cur]));
   std::vector<double> h(6 * c->nred);
-  CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  dvbm_status s = wait_stream(c);
+  dvbm_status s = drain_then_copy(c, h.data(), c->partial, h.size() * sizeof(double));
   if (s != DVBM_OK) return s;
   double acc[5] = {0, 0, 0, 0, 0};
   for (int b = 0; b < c->nred; ++b)
@@ -449,12 +472,16 @@ extern "C" dvbm_status dvbm_get_state(dvbm_ctx* c, void* buf, size_t bytes, int 
   void* dev = buf;
   if (!on_device) CUDA_TRY(c, cudaMalloc(&dev, pb));
   cudaError_t e = launch_pack(c->storage, c->buf[c->cur], dev, 1, c->G, c->npop, c->stream);
-  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(buf, dev, pb, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync((char*)buf + pb, &c->steps, 8, on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
-                        c->stream);
-  dvbm_status s = e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "get_state: %s", cudaGetErrorString(e));
-  if (!on_device) cudaFree(dev);
+  dvbm_status s = e == cudaSuccess ? DVBM_OK : fail(c, DVBM_ECUDA, "get_state: %s", cudaGetErrorString(e));
+  if (s == DVBM_OK && !on_device) {
+    s = drain_then_copy(c, buf, dev, pb);
+    if (s == DVBM_OK) std::memcpy((char*)buf + pb, &c->steps, 8);
+  } else if (s == DVBM_OK) {
+    s = wait_stream(c);
+    if (s == DVBM_OK) e = cudaMemcpyAsync((char*)buf + pb, &c->steps, 8, cudaMemcpyHostToDevice, c->stream);
+    if (s == DVBM_OK) s = e == cudaSuccess ? wait_stream(c) : fail(c, DVBM_ECUDA, "get_state: %s", cudaGetErrorString(e));
+  }
+  if (!on_device) release_temporary(c, dev, s);
   return s;
 }
 
@@ -471,16 +498,24 @@ extern "C" dvbm_status dvbm_set_state(dvbm_ctx* c, const void* buf, size_t bytes
   if (!on_device) {
     CUDA_TRY(c, cudaMalloc(&dev, pb));
   }
+  // a copy from pageable host memory may wait for the stream: drain it first, under the limit
+  dvbm_status s = on_device ? DVBM_OK : wait_stream(c);
   cudaError_t e = cudaSuccess;
-  if (!on_device) e = cudaMemcpyAsync(dev, buf, pb, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = launch_pack(c->storage, c->buf[c->cur], dev, 0, c->G, c->npop, c->stream);
+  if (s == DVBM_OK && !on_device) e = cudaMemcpyAsync(dev, buf, pb, cudaMemcpyHostToDevice, c->stream);
+  if (s == DVBM_OK && e == cudaSuccess) e = launch_pack(c->storage, c->buf[c->cur], dev, 0, c->G, c->npop, c->stream);
+  // a new state: an instability raised by the replaced one no longer applies
+  if (s == DVBM_OK && e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(unsigned int), c->stream);
+  if (s == DVBM_OK)
+    s = e == cudaSuccess ? fill_ghosts(c, c->buf[c->cur]) : fail(c, DVBM_ECUDA, "set_state: %s", cudaGetErrorString(e));
   long long st = 0;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&st, (const char*)buf + pb, 8, on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
-                        c->stream);
-  dvbm_status s = e == cudaSuccess ? fill_ghosts(c, c->buf[c->cur]) : fail(c, DVBM_ECUDA, "set_state: %s", cudaGetErrorString(e));
-  if (s == DVBM_OK) s = wait_stream(c);
-  if (!on_device) cudaFree(dev);
+  if (s == DVBM_OK) {
+    if (on_device) s = drain_then_copy(c, &st, (const char*)buf + pb, 8);
+    else {
+      std::memcpy(&st, (const char*)buf + pb, 8);
+      s = wait_stream(c);
+    }
+  }
+  if (!on_device) release_temporary(c, dev, s);
   if (s != DVBM_OK) return s;
   c->steps = st;
   c->initialised = true;
@@ -528,9 +563,9 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
   auto cleanup = [&]() {
     for (int i = 0; i < 2; ++i) if (lam[i]) c->pool.push_back(lam[i]);
     for (void* p : seg) c->pool.push_back(p);
-    if (part) cudaFree(part);
-    if (codes) cudaFree(codes);
-    if (moms) cudaFree(moms);
+    if (part) release_temporary(c, part, s);
+    if (codes) release_temporary(c, codes, s);
+    if (moms) release_temporary(c, moms, s);
   };
   for (int i = 0; i < 2 && s == DVBM_OK; ++i) s = take_buffer(c, &lam[i]);
   for (int i = 0; i < k + (coded ? 1 : 0) && s == DVBM_OK; ++i) {
@@ -581,13 +616,9 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
     e = launch_adjoint_init((const double*)lam[a], F0, F0 + ncell, F0 + 2 * ncell, F0 + 3 * ncell, g_rho0, g_ux0,
                             g_uy0, g_T0, part + slot * nblk * 4, c->G, c->P, c->M, c->stream);
   ++slot;
-  std::vector<double> h;
-  if (e == cudaSuccess) {
-    h.resize(slot * nblk * 4);
-    e = cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  }
   if (e != cudaSuccess) { cleanup(); return fail(c, DVBM_ECUDA, "adjoint: %s", cudaGetErrorString(e)); }
-  s = wait_stream(c);
+  std::vector<double> h(slot * nblk * 4);
+  s = drain_then_copy(c, h.data(), part, h.size() * sizeof(double));
   cleanup();
   if (s != DVBM_OK) return s;
   // slot 0: final read-out (gm1 adjoint per block); slots 1..n: steps (dt_mu, Pr, gm1, epsf);
@@ -621,5 +652,6 @@ extern "C" void dvbm_destroy(dvbm_ctx* c) {
   for (void* p : c->pool) cudaFree(p);
   if (c->init_fields) cudaFree(c->init_fields);
   if (c->stage) cudaFree(c->stage);
+  for (void* p : c->in_flight) cudaFree(p);
   delete c;
 }

@@ -124,8 +124,13 @@ dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, double Pr, 
  * dt = cfl min(dx, dy) / max(|u| + sqrt(gamma R T)) over these fields unless
  * opts.dt > 0.  Resets the step counter.  Host fields (on_device = 0) pass
  * through a staging buffer of 4 Nx Ny doubles that the context allocates on
- * first use and keeps until dvbm_destroy.  Errors: EINVAL (null pointer,
- * rho <= 0 or T <= 0 or non-finite input: DVBM_EINVAL), ENOMEM, ECUDA. */
+ * first use and keeps until dvbm_destroy.  The time step must respect the
+ * explicit scheme's limits: max_i |v_i| dt / min(dx, dy) <= 1 (the fastest
+ * population crosses at most one cell per step) and dt <= min(tau1, tau2) =
+ * mu / p_max * min(1, 1/Pr) at the largest pressure p = rho R T of the given
+ * fields (forward-Euler relaxation); otherwise EINVAL, and the context is left
+ * as it was.  Errors: EINVAL (null pointer, rho <= 0 or T <= 0 or non-finite
+ * input, dt beyond the limits), ENOMEM, ECUDA, ETIMEOUT. */
 dvbm_status dvbm_init(dvbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
                       const double* T, int on_device);
 
@@ -158,7 +163,9 @@ size_t dvbm_state_bytes(const dvbm_ctx* ctx);
 /* Copy the current state out / in (checkpoint / resume).  bytes must equal
  * dvbm_state_bytes.  set_state refills the ghost layers and clears the
  * instability flag (a run that returned EUNSTABLE resumes from a restored
- * state); the restored state is checked by the next step like any other. */
+ * state); the restored state is checked by the next step like any other.
+ * Without a prior dvbm_init, set_state takes dt = opts.dt (> 0, else
+ * ESTATE), subject to the one-cell-per-step limit of dvbm_init (else EINVAL). */
 dvbm_status dvbm_get_state(dvbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 dvbm_status dvbm_set_state(dvbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
 

@@ -96,6 +96,25 @@ static double node(const dvbm_ctx* c, int k) {
   return xi_of(k);
 }
 
+// Limits of the explicit scheme on the fixed time step: the fastest population crosses at most
+// one cell per step (the upwind stencil's domain of dependence must contain the characteristic),
+// and forward-Euler relaxation takes dt <= the shortest relaxation time, min(tau1, tau2) =
+// mu / p * min(1, 1/Pr) at the largest pressure p = rho R T of the initial field.  pmax <= 0: no
+// field known (set_state without dvbm_init), the relaxation limit is not checked.
+static dvbm_status check_dt(dvbm_ctx* c, double dt, double pmax) {
+  double xi = 0.0;
+  for (int k = 0; k < 5; ++k) xi = std::fmax(xi, std::fabs(node(c, k)));
+  const double courant = dt * c->M.c * xi / std::fmin(c->opts.Lx / c->Nx, c->opts.Ly / c->Ny);
+  if (!(courant <= 1.0))
+    return fail(c, DVBM_EINVAL, "dt = %g moves the fastest population %.3g cells per step (limit 1)", dt, courant);
+  if (pmax > 0) {
+    const double tau_min = c->mu / pmax * std::fmin(1.0, 1.0 / c->Pr);
+    if (!(dt <= tau_min))
+      return fail(c, DVBM_EINVAL, "dt = %g exceeds the shortest relaxation time %g of the initial field", dt, tau_min);
+  }
+  return DVBM_OK;
+}
+
 static void set_step_factors(dvbm_ctx* c) {
   const double dx = c->opts.Lx / c->Nx, dy = c->opts.Ly / c->Ny;
   for (int k = 0; k < 5; ++k) {
@@ -365,14 +384,21 @@ extern "C" dvbm_status dvbm_init(dvbm_ctx* c, const double* rho, const double* u
   if (s != DVBM_OK) return s;
   const long long n = (long long)c->Nx * c->Ny;
   CUDA_TRY(c, launch_speed(F.p[0], F.p[1], F.p[2], F.p[3], n, c->partial, c->nred, c->M, c->stream));
-  std::vector<double> h(2 * c->nred);
+  std::vector<double> h(3 * c->nred);
   s = drain_then_copy(c, h.data(), c->partial, h.size() * sizeof(double));
   if (s != DVBM_OK) return s;
-  double vmax = 0.0, bad = 0.0;
-  for (int b = 0; b < c->nred; ++b) { vmax = std::fmax(vmax, h[2 * b]); bad += h[2 * b + 1]; }
+  double vmax = 0.0, bad = 0.0, pmax = 0.0;
+  for (int b = 0; b < c->nred; ++b) {
+    vmax = std::fmax(vmax, h[3 * b]);
+    bad += h[3 * b + 1];
+    pmax = std::fmax(pmax, h[3 * b + 2]);
+  }
   if (bad > 0) return fail(c, DVBM_EINVAL, "%.0f cells with rho <= 0, T <= 0 or non-finite values", bad);
-  if (c->opts.dt > 0) c->dt = c->opts.dt;
-  else c->dt = c->opts.cfl * std::fmin(c->opts.Lx / c->Nx, c->opts.Ly / c->Ny) / vmax;
+  const double dt = c->opts.dt > 0 ? c->opts.dt
+                                   : c->opts.cfl * std::fmin(c->opts.Lx / c->Nx, c->opts.Ly / c->Ny) / vmax;
+  s = check_dt(c, dt, pmax);  // before any change to the context
+  if (s != DVBM_OK) return s;
+  c->dt = dt;
   set_step_factors(c);
   c->cur = 0;
   CUDA_TRY(c, l_init(c, c->buf[0], F.p));
@@ -490,6 +516,8 @@ extern "C" dvbm_status dvbm_set_state(dvbm_ctx* c, const void* buf, size_t bytes
   if (bytes != dvbm_state_bytes(c)) return fail(c, DVBM_EINVAL, "state buffer must be %zu bytes", dvbm_state_bytes(c));
   if (!(c->dt > 0)) {
     if (!(c->opts.dt > 0)) return fail(c, DVBM_ESTATE, "set_state needs dt: call dvbm_init first or set opts.dt");
+    const dvbm_status sd = check_dt(c, c->opts.dt, 0.0);
+    if (sd != DVBM_OK) return sd;
     c->dt = c->opts.dt;
     set_step_factors(c);
   }

@@ -8,7 +8,8 @@
 //             mirrors interior cell k (k = 1, 2)
 //  k_moments  rho, u, T fields
 //  k_totals   per-block sums of mass, momentum, total energy (+ bad-cell count)
-//  k_speed    per-block maximum of |u| + sqrt(gamma R T) for the CFL rule
+//  k_speed    per-block maxima of |u| + sqrt(gamma R T) (CFL rule) and of p = rho R T
+//             (shortest relaxation time), and a bad-input count
 //  k_pack     padded <-> packed [50][Ny][Nx] state copies
 #include "dvbm_device.cuh"
 #include "dvbm_cellmom.cuh"
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256) k_totals(const S* __restrict__ src, doubl
 __global__ void __launch_bounds__(256) k_speed(const double* __restrict__ rho, const double* __restrict__ ux,
                                                const double* __restrict__ uy, const double* __restrict__ T,
                                                long long n, double* partial, Macro M) {
-  double mx = 0.0, bad = 0.0;
+  double mx = 0.0, bad = 0.0, pm = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double r = rho[i], a = ux[i], b = uy[i], t = T[i];
     if (!(r > 0.0) || !(t > 0.0) || !(fabs(a) < 1e300) || !(fabs(b) < 1e300) || !(r < 1e300) || !(t < 1e300)) {
@@ -171,21 +172,25 @@ __global__ void __launch_bounds__(256) k_speed(const double* __restrict__ rho, c
       continue;
     }
     mx = fmax(mx, sqrt(a * a + b * b) + sqrt(M.gamma * M.R * t));
+    pm = fmax(pm, r * M.R * t);
   }
-  __shared__ double sm[256], sb[256];
+  __shared__ double sm[256], sb[256], sp[256];
   sm[threadIdx.x] = mx;
   sb[threadIdx.x] = bad;
+  sp[threadIdx.x] = pm;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) {
       sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
       sb[threadIdx.x] += sb[threadIdx.x + w];
+      sp[threadIdx.x] = fmax(sp[threadIdx.x], sp[threadIdx.x + w]);
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = sm[0];
-    partial[2 * blockIdx.x + 1] = sb[0];
+    partial[3 * blockIdx.x] = sm[0];
+    partial[3 * blockIdx.x + 1] = sb[0];
+    partial[3 * blockIdx.x + 2] = sp[0];
   }
 }
 

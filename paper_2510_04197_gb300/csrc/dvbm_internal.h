@@ -32,7 +32,8 @@ cudaError_t launch_moments(int storage, const void* src, double* rho, double* ux
 // per-block partial sums: out[blk*6 + {mass, momx, momy, energy, bad, 0}]
 cudaError_t launch_totals(int storage, const void* src, double* partial, int nblocks, const Geom& G,
                           const Phys& P, const Macro& M, cudaStream_t st);
-// per-block maxima of |u| + sqrt(gamma R T) and a bad-input count: out[blk*2 + {max, bad}]
+// per-block maxima of |u| + sqrt(gamma R T) and of p = rho R T, and a bad-input count:
+// out[blk*3 + {max speed, bad, max p}]
 cudaError_t launch_speed(const double* rho, const double* ux, const double* uy, const double* T, long long n,
                          double* partial, int nblocks, const Macro& M, cudaStream_t st);
 cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G, int npop,

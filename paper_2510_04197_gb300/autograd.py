@@ -31,17 +31,24 @@ class DVBMFunction(torch.autograd.Function):
         sim.step(int(nsteps))
         m = sim.moments()
         ctx.sim = sim
+        # gradients go back on the devices and dtypes of the inputs
+        ctx.like = [(t.device, t.dtype) for t in (rho0, ux0, uy0, T0, params)]
         return m["rho"], m["T"]
 
     @staticmethod
     def backward(ctx, g_rho, g_T):
         sim = ctx.sim
+        if sim is None:
+            raise RuntimeError("DVBMFunction supports one backward pass per forward: its recorded run "
+                               "is released after the adjoint")
         g = sim.adjoint(g_rho.contiguous() if g_rho is not None else None,
                         g_T.contiguous() if g_T is not None else None)
         gp = torch.tensor([g["mu"], g["Pr"], g["gamma"]], dtype=torch.float64)
         sim.close()
         ctx.sim = None
-        return g["rho0"], g["ux0"], g["uy0"], g["T0"], gp, None, None
+        out = [g["rho0"], g["ux0"], g["uy0"], g["T0"], gp]
+        out = [t.to(device=dev, dtype=dt) for t, (dev, dt) in zip(out, ctx.like)]
+        return (*out, None, None)
 
 
 def run(rho0, ux0, uy0, T0, params, nsteps, **options):

@@ -143,6 +143,35 @@ def test_autograd_function_end_to_end(D):
     assert abs(float(params.grad[0]) - g["mu"]) < 1e-10 * abs(g["mu"])
 
 
+def test_autograd_gradients_follow_input_devices(D):
+    """Gradients come back on the devices of the inputs (fields on the host and
+    parameters on the GPU, and the reverse), equal between the two placements;
+    a second backward through the same forward is refused."""
+    from paper_2510_04197_gb300.autograd import run
+    F = I.random_smooth(16, 16, seed=8, amp=0.05, Ma=0.3)
+    rho_t, T_t = targets(16, 16)
+
+    def loss(dev_f, dev_p):
+        fields = [torch.tensor(getattr(F, k), device=dev_f, requires_grad=True) for k in ("rho", "ux", "uy", "T")]
+        params = torch.tensor([2e-3, 0.71, 1.4], dtype=DT, device=dev_p, requires_grad=True)
+        rho, T = run(*fields, params, 9, dt=2e-4)
+        L = 0.5 / 256 * (((rho - torch.tensor(rho_t, device=rho.device)) ** 2).sum() +
+                         ((T - torch.tensor(T_t, device=T.device)) ** 2).sum())
+        return L, fields, params
+
+    L1, f1, p1 = loss("cuda", "cpu")
+    L1.backward()
+    L2, f2, p2 = loss("cpu", "cuda")
+    L2.backward(retain_graph=True)
+    assert all(t.grad.device.type == "cuda" for t in f1) and p1.grad.device.type == "cpu"
+    assert all(t.grad.device.type == "cpu" for t in f2) and p2.grad.device.type == "cuda"
+    for a, b in zip(f1, f2):
+        assert torch.allclose(a.grad.cpu(), b.grad, rtol=1e-13, atol=0)
+    assert torch.allclose(p1.grad, p2.grad.cpu(), rtol=1e-13, atol=0)
+    with pytest.raises(RuntimeError, match="one backward pass"):
+        L2.backward()
+
+
 def test_adjoint_requires_recording(D):
     F = I.random_smooth(8, 8, seed=1)
     sim = D.Simulation(8, 8, 0.71, 1.4, 2e-3, dt=2e-4)

@@ -142,12 +142,15 @@ dvbm_status dvbm_step(dvbm_ctx* ctx, int n);
 /* rho, u_x, u_y, T of the current state (Sec. II.D.1 moments, T from
  * Eq. Total_energy_MB).  Any output pointer may be NULL to skip it.  Host
  * outputs (on_device = 0) go through the context's staging buffer (see
- * dvbm_init); the call returns once they are written. */
+ * dvbm_init); the call returns once they are written.
+ * Errors: EINVAL, ESTATE (no state yet), ENOMEM, ECUDA, ETIMEOUT. */
 dvbm_status dvbm_moments(dvbm_ctx* ctx, double* rho, double* ux, double* uy, double* T,
                          int on_device);
 
 /* Domain totals out[0..3] = mass, x-momentum, y-momentum, total energy
- * (sum over cells times dx dy).  Synchronous. */
+ * (sum over cells times dx dy).  Synchronous.  EUNSTABLE when a cell of the
+ * current state has rho <= 0, T <= 0 or a non-finite value (out is filled
+ * all the same).  Errors: EINVAL, ESTATE, EUNSTABLE, ECUDA, ETIMEOUT. */
 dvbm_status dvbm_totals(dvbm_ctx* ctx, double out[4]);
 
 /* Size in bytes of a state snapshot: the population planes [c][Ny][Nx] of the
@@ -165,7 +168,9 @@ size_t dvbm_state_bytes(const dvbm_ctx* ctx);
  * instability flag (a run that returned EUNSTABLE resumes from a restored
  * state); the restored state is checked by the next step like any other.
  * Without a prior dvbm_init, set_state takes dt = opts.dt (> 0, else
- * ESTATE), subject to the one-cell-per-step limit of dvbm_init (else EINVAL). */
+ * ESTATE), subject to the one-cell-per-step limit of dvbm_init (else EINVAL).
+ * Host buffers (on_device = 0) pass through a temporary device buffer.
+ * Errors: EINVAL (null pointer, wrong size), ESTATE, ENOMEM, ECUDA, ETIMEOUT. */
 dvbm_status dvbm_get_state(dvbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 dvbm_status dvbm_set_state(dvbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
 
@@ -184,7 +189,7 @@ dvbm_status dvbm_record(dvbm_ctx* ctx, int every);
  * array g_params, dL/dmu, dL/dPr, dL/dgamma.  Each checkpoint segment is
  * recomputed once, then stepped backwards with the hand-written adjoint step
  * kernel.  The state of the context is left unchanged.  Synchronous.
- * Errors: ESTATE (no recording), EINVAL, ENOMEM, ECUDA. */
+ * Errors: ESTATE (no recording), EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
 dvbm_status dvbm_adjoint(dvbm_ctx* ctx, const double* dL_drho, const double* dL_dT, double* g_rho0,
                          double* g_ux0, double* g_uy0, double* g_T0, double g_params[3]);
 

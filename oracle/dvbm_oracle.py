@@ -41,6 +41,13 @@ Where the paper is silent or garbled this module takes these readings: the
 D2Q25 weights carry a /60; the third-order QE moment is the symmetric tensor
 whose contraction equals the heat-flux constraint; b = 0 gives a zero limited
 slope; the time step is fixed from the initial field.
+
+Parity unpinned: the components of the third-order quasi-equilibrium moment
+M3(f*) beyond its contraction (``_S_operator``, used by ``quasi_equilibria``).
+The paper calls that tensor slightly over-constrained and fixes only its
+contraction, through the heat-flux constraints; the contraction is pinned by
+the tests, the remaining components are this module's reading, which the
+CUDA path shares as a reading, not as code.
 """
 from __future__ import annotations
 
@@ -376,7 +383,8 @@ def _S_operator(u, A, tup):
     - tr(A)/(D+2) [u_a d_bc]_cyc whose contraction over (b, c) equals 2 (A u)_a.
     This is the reading of the tensor "2 u (x) A" in Table I (split II, third
     order of f*): the heat-flux constraints (Eqs. QE_Pr<1_quasiconserved,
-    QE_Pr>1_conserved) fix only its contraction 2 (A u)_a."""
+    QE_Pr>1_conserved) fix only its contraction 2 (A u)_a.  Parity unpinned
+    beyond that contraction."""
     a, b, c = tup
     trA = A[(0, 0)] + A[(1, 1)]
     cyc_uA = u[a] * A[(b, c)] + u[b] * A[(a, c)] + u[c] * A[(a, b)]

@@ -3,7 +3,6 @@
 oracle's forward map, element by element -- and (2) central finite
 differences of the CUDA forward map itself.  Loss:
 L = 1/(2N) sum[(rho_n - rho_t)^2 + (T_n - T_t)^2], dt held fixed."""
-import math
 
 import numpy as np
 import pytest

@@ -5,7 +5,6 @@ Each test compares the oracle with a closed form, a textbook/library routine
 Maxwellian), a constraint equation printed in the paper, or an invariant that
 a dropped term, a wrong sign or a transposed index would break.
 """
-import itertools
 import math
 import re
 

@@ -175,7 +175,12 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
   c->opts = o;
   for (int s = 0; s < 4; ++s) c->bcs[s] = b[s];
   c->stream = (cudaStream_t)stream;
-  cudaGetDevice(&c->device);
+  const cudaError_t ed = cudaGetDevice(&c->device);
+  if (ed != cudaSuccess) {
+    cudaGetLastError();
+    delete c;  // nothing allocated yet
+    return fail(nullptr, DVBM_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(ed));
+  }
   c->elem = storage == DVBM_FP64 ? 8 : 4;
   const int align = 128 / (int)c->elem;  // elements per 128 B
   c->G.Nx = Nx; c->G.Ny = Ny;
@@ -215,10 +220,16 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
     if (e != cudaSuccess) {
       cudaGetLastError();
       dvbm_destroy(c);
-      return fail(nullptr, DVBM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+      return fail(nullptr, e == cudaErrorMemoryAllocation ? DVBM_ENOMEM : DVBM_ECUDA,
+                  "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
   }
-  c->nred = 4 * 152;
+  int sms = 0;  // reduction grids: four blocks per SM (grid-stride loops, any count is correct)
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  c->nred = 4 * sms;
   if (cudaMalloc(&c->flag, sizeof(unsigned int)) != cudaSuccess ||
       cudaMalloc(&c->partial, sizeof(double) * 6 * c->nred) != cudaSuccess) {
     cudaGetLastError();

@@ -72,3 +72,16 @@ def test_null_context_calls_fail_cleanly(L):
     lib.dvbm_destroy(None)
     st = lib.dvbm_create(None, 0, 16, 16, 0.71, 1.4, 1e-3, None, 0, None, None)
     assert st == L.EINVAL
+
+
+def test_create_without_a_usable_device_reports_ecuda(L):
+    """Valid arguments on a host with no usable CUDA device: dvbm_create
+    returns ECUDA (not an allocation failure), leaves *out NULL and says why."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p(1)
+    st = L.lib().dvbm_create(ctypes.byref(h), 0, 16, 16, 0.71, 1.4, 1e-3, None, 0, None, None)
+    assert st == L.ECUDA, st
+    assert not h.value
+    assert b"no usable CUDA device" in L.lib().dvbm_last_error(None)

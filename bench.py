@@ -80,6 +80,23 @@ def kernel_source_hash(sources=STEP_KERNEL_SOURCES):
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (a job takes as long as its slowest rank);
+    x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank, steps, world, seconds):
+    """Cell updates of all ranks (one independent grid each) per second, in
+    millions."""
+    return cells_per_rank * steps * world / seconds / 1e6
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as fh:
@@ -335,12 +352,8 @@ def main():
         barrier()
         if sampler:
             clocks = sampler.stop()
-        tmax = total_ms
-        if dist:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tmax = float(t.item())
-        mlups = N * N * args.steps * world / (tmax * 1e-3) / 1e6
+        tmax = max_over_ranks(total_ms, dist, "cuda")
+        mlups = whole_job_mlups(N * N, args.steps, world, tmax * 1e-3)
         tot = sim.totals()  # also raises if the run went unstable
         results[storage] = {"mlups": mlups, "ms_per_step": tmax / args.steps,
                             "kernel_ms": statistics.mean(per), "totals": tot}
@@ -392,13 +405,9 @@ def main():
         import ctypes
         st = dvbm.lib().dvbm_moments(sim._h, *[ctypes.c_void_p(outs[k].data_ptr()) for k in ("rho", "ux", "uy", "T")], 0)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         assert st == 0
-        e2e = {"value": N * N * args.steps * world / el / 1e6, "unit": "MLUPS",
+        e2e = {"value": whole_job_mlups(N * N, args.steps, world, el), "unit": "MLUPS",
                "h2d_bytes_per_step": 4 * 8 * N * N / args.steps, "d2h_bytes_per_step": 4 * 8 * N * N / args.steps,
                "note": "init from host fields + K steps + moments to host, per-step bytes = total / K"}
         sim.close()

@@ -91,6 +91,15 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
+def conservation_drift(t0, t1, steps):
+    """Change of the domain totals (mass, x/y momentum, energy) over a run:
+    mass and energy relative to their initial values, momentum per unit
+    initial mass (a velocity, in units of sqrt(R T_ref))."""
+    m0 = t0[0]
+    return {"steps": steps, "mass": (t1[0] - t0[0]) / m0, "momentum_x": (t1[1] - t0[1]) / m0,
+            "momentum_y": (t1[2] - t0[2]) / m0, "energy": (t1[3] - t0[3]) / t0[3]}
+
+
 def whole_job_mlups(cells_per_rank, steps, world, seconds):
     """Cell updates of all ranks (one independent grid each) per second, in
     millions."""
@@ -339,6 +348,7 @@ def main():
         sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, storage=1 if storage == "fp32dev" else 0, check_every=-1,
                               lattice=dvbm.D2Q16_SPLIT_I if storage == "d2q16" else dvbm.D2Q25_SPLIT_II)
         sim.init(*fields)
+        tot0 = sim.totals()  # outside the timed region: the conservation drift of the whole run
         sim.step(args.warmup)
         torch.cuda.synchronize()
         sampler = ClockSampler(local) if storage == "fp64" else None
@@ -356,7 +366,8 @@ def main():
         mlups = whole_job_mlups(N * N, args.steps, world, tmax * 1e-3)
         tot = sim.totals()  # also raises if the run went unstable
         results[storage] = {"mlups": mlups, "ms_per_step": tmax / args.steps,
-                            "kernel_ms": statistics.mean(per), "totals": tot}
+                            "kernel_ms": statistics.mean(per), "totals": tot,
+                            "drift": conservation_drift(tot0, tot, args.warmup + args.steps)}
         sim.close()
         del sim
         torch.cuda.empty_cache()
@@ -445,12 +456,12 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(N),
             "roofline": roofline, "roofline_hbm": roofline_hbm, "clocks": clocks,
             "gpu_launches": 2 * args.steps,
-            "kernel_ms_per_step": r64["kernel_ms"]}
+            "kernel_ms_per_step": r64["kernel_ms"], "conservation_drift": r64["drift"]}
     if "fp32dev" in results:
         r32 = results["fp32dev"]
         g32 = BYTES_PER_CELL["fp32dev"] * N * N / (r32["kernel_ms"] * 1e-3) / 1e9
         line["fp32dev"] = {"value": r32["mlups"], "unit": "MLUPS", "ms_per_step": r32["ms_per_step"],
-                           "dtype": "f32 storage / f64 moments+equilibria",
+                           "dtype": "f32 storage / f64 moments+equilibria", "conservation_drift": r32["drift"],
                            "roofline_hbm": {"bound": "hbm", "achieved": g32, "peak": hbm_peak, "unit": "GB/s",
                                             "frac": g32 / hbm_peak, "frac_of_8tbs": g32 / NOMINAL_HBM_GBS}}
         t32 = profile_traffic("k_step_fp32dev")
@@ -460,6 +471,7 @@ def main():
         g16 = BYTES_PER_CELL["d2q16"] * N * N / (r16["kernel_ms"] * 1e-3) / 1e9
         line["d2q16_split_I"] = {"value": r16["mlups"], "unit": "MLUPS", "ms_per_step": r16["ms_per_step"],
                                  "dtype": "f64", "workload": "same flow, total-energy split (I) on D2Q16",
+                                 "conservation_drift": r16["drift"],
                                  "roofline_hbm": {"bound": "hbm", "achieved": g16, "peak": hbm_peak, "unit": "GB/s",
                                                   "frac": g16 / hbm_peak, "frac_of_8tbs": g16 / NOMINAL_HBM_GBS}}
         t16 = profile_traffic("k_step16")

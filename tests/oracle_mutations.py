@@ -22,6 +22,10 @@ MUTATIONS = [
     "wall_ghosts_swapped",        # ghost 1 mirrors interior cell 2 and vice versa
     "zero_gradient_second_cell",  # zero-gradient ghosts copy the second cell
     "face_areas_swapped",         # dy on y-faces and dx on x-faces
+    "split1_energy_with_kinetic_part",  # split I: E = sum g + v^2/2 f instead of sum g
+    "downwind_faces",             # faces reconstructed from the downwind side
+    "prandtl_branch_ignored",     # Pr > 1 relaxed with the Pr < 1 mapping of tau1, tau2
+    "d2q16_weights_swapped",      # D2Q16 inner and outer 1-D weights exchanged
 ]
 
 
@@ -101,6 +105,35 @@ def _apply(O, name):
             g2 = O.Grid(grid.Nx, grid.Ny, grid.Ly * grid.Nx / grid.Ny, grid.Lx * grid.Ny / grid.Nx, grid.bcs)
             return f0(lat, P, g2, fpx, fpy)
         O.advective_term = adv
+    elif name == "split1_energy_with_kinetic_part":
+        f0 = O.macroscopic
+
+        def mac1(lat, P, f, g):
+            rho, ux, uy, T, E = f0(lat, P, f, g)
+            if P.split != "I":
+                return rho, ux, uy, T, E
+            v2 = (lat.vx * lat.vx + lat.vy * lat.vy).view((-1,) + (1,) * (f.dim() - 1))
+            E = g.sum(0) + (0.5 * v2 * f).sum(0)
+            return rho, ux, uy, (E / rho - 0.5 * (ux * ux + uy * uy)) / P.Cv(), E
+        O.macroscopic = mac1
+    elif name == "downwind_faces":
+        f0 = O.face_values
+        O.face_values = lambda Fm2, Fm1, F0, Fp1, vpos, beta: f0(Fm2, Fm1, F0, Fp1, ~vpos, beta)
+    elif name == "prandtl_branch_ignored":
+        def tau(P, rho, T):
+            t1 = P.mu / (rho * P.R * T)
+            return t1, t1 / P.Pr
+        O.relaxation_times = tau
+    elif name == "d2q16_weights_swapped":
+        f0 = O.Lattice.__init__
+
+        def init(self, *a, **k):
+            f0(self, *a, **k)
+            if self.Q == 16:
+                w1 = [self.w1[1], self.w1[0], self.w1[3], self.w1[2]]
+                self.w1 = w1
+                self.w = torch.tensor([w1[p] * w1[q] for p in range(4) for q in range(4)], dtype=O.DT)
+        O.Lattice.__init__ = init
     else:
         raise ValueError(f"unknown mutation {name}")
 

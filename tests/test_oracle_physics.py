@@ -72,6 +72,7 @@ def run_modes_split(Pr, gamma, Ma, Nx=32, Ny=2, mu=0.01, dt=2e-4, n1=600, n2=100
             out += [d.real, d.imag]
         return np.concatenate(out)
 
+    assert np.isfinite(c1).all() and all(np.isfinite(c).all() for _, c in hist), "the run left the finite range"
     alpha = so.least_squares(resid, [nu / Pr]).x[0]
     nu_fit = -np.log(abs(hist[-1][1][2]) / abs(c1[2])) / hist[-1][0] / k ** 2
     return nu_fit, alpha
@@ -139,6 +140,7 @@ def run_acoustic(Pr, gamma, split, Nx=32, Ny=2, mu=0.01, dt=2e-4, n1=600, n2=100
             out += [d.real, d.imag]
         return np.concatenate(out)
 
+    assert np.isfinite(c1).all() and all(np.isfinite(c).all() for _, c in hist), "the run left the finite range"
     return so.least_squares(resid, [mu * (3 - gamma)]).x[0]
 
 

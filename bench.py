@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-d2q16", action="store_true")
     ap.add_argument("--no-workloads", action="store_true")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="the oracle's CPU baseline table on one and on all host threads (one JSON line)")
     ap.add_argument("--sweep", action="store_true",
                     help="throughput sweep over grid size, rms Mach number and storage form (one JSON line)")
     return ap.parse_args()
@@ -183,26 +185,98 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(N_sample, steps=30, warmup=1):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    a periodic N_sample^2 multimode field of the same recipe, ``warmup``
-    untimed steps, then ``steps`` timed steps (512^2 x 30 steps: about 12 s
-    on 16 host cores)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_mlups(N, steps, warmup=1, threads=None, fields=None, P_kw=None, cfl=0.01):
+    """MLUPS of the FP64 CPU oracle, as it stands, on an N^2 periodic field
+    (default: the bench's multimode recipe), ``warmup`` untimed steps then
+    ``steps`` timed; ``threads`` = torch intra-op threads (None: all)."""
     import torch
     from oracle import dvbm_oracle as O
     from paper_2510_04197_gb300 import inputs
-    F = inputs.multimode(N_sample, seed=0, rms_Ma=0.3)
+    F = fields if fields is not None else inputs.multimode(N, seed=0, rms_Ma=0.3)
     t = lambda a: torch.tensor(a, dtype=torch.float64)
-    P = O.Params(Pr=0.71, gamma=1.4, mu=5e-5)
-    sim = O.Simulation(O.Grid(N_sample, N_sample), P, t(F.rho), t(F.ux), t(F.uy), t(F.T), cfl=0.01)
-    sim.run(warmup)
-    t0 = time.perf_counter()
-    sim.run(steps)
-    el = time.perf_counter() - t0
-    mlups = N_sample * N_sample * steps / el / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+    P = O.Params(**(P_kw or dict(Pr=0.71, gamma=1.4, mu=5e-5)))
+    old = torch.get_num_threads()
+    if threads:
+        torch.set_num_threads(threads)
+    try:
+        Ny, Nx = F.rho.shape
+        sim = O.Simulation(O.Grid(Nx, Ny, F.Lx, F.Ly), P, t(F.rho), t(F.ux), t(F.uy), t(F.T), cfl=cfl)
+        sim.run(warmup)
+        t0 = time.perf_counter()
+        sim.run(steps)
+        el = time.perf_counter() - t0
+        used = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(old)
+    return Nx * Ny * steps / el / 1e6, el, used
+
+
+def cpu_baseline(N_sample, steps=30, warmup=1):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    a periodic N_sample^2 multimode field of the same recipe, ``warmup``
+    untimed steps, then ``steps`` timed steps on all host threads (512^2 x 30
+    steps: about 12 s on 16 host cores); beside it one thread on a 256^2 x 4
+    step sample."""
+    v, el, used = oracle_mlups(N_sample, steps, warmup)
+    v1, el1, _ = oracle_mlups(256, 4, 1, threads=1)
+    return {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{N_sample}x{N_sample} periodic multimode (same recipe), {steps} FP64 steps after {warmup} warm-up, "
-                      f"{el:.1f} s"}
+                      f"{el:.1f} s on {used} threads",
+            "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1,
+                              "sample": f"256x256, 4 FP64 steps after 1 warm-up, {el1:.1f} s"}}
+
+
+def cpu_table():
+    """The oracle's baseline table (one JSON line): config 1 (64^2 wave decay,
+    1000 steps) and the 1024^2 multimode flow (10 steps), each on one thread
+    and on all host threads, with the CPU model.  Minutes of CPU time."""
+    import torch
+    from paper_2510_04197_gb300 import inputs
+    rows = []
+    wave = inputs.wave_decay(64, 64, Ma=0.1, amp=1e-3)
+    for threads in (1, None):
+        v, el, used = oracle_mlups(64, 1000, 1, threads, fields=wave, P_kw=dict(Pr=0.71, gamma=1.4, mu=0.01))
+        rows.append({"workload": "64^2 wave decay (config 1), 1000 steps", "threads": used, "mlups": v, "s": el})
+        v, el, used = oracle_mlups(1024, 10, 1, threads)
+        rows.append({"workload": "1024^2 periodic multimode, 10 steps", "threads": used, "mlups": v, "s": el})
+    print(json.dumps({"cpu_table": rows, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                      "torch_threads": torch.get_num_threads(), "kind": "oracle"}), flush=True)
+
+
+def fp64_probe():
+    """Measured FP64 FMA peak of this GPU (libdvbm_probe.so, CUDA events)."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2510_04197_gb300", "libdvbm_probe.so")
+    try:
+        L = ctypes.CDLL(path)
+        L.dvbm_probe_fp64_fma.restype = ctypes.c_int
+        tf, ms = ctypes.c_double(0), ctypes.c_double(0)
+        rc = L.dvbm_probe_fp64_fma(5, ctypes.byref(tf), ctypes.byref(ms))
+        if rc == 0:
+            return {"tflops": tf.value, "best_ms": ms.value,
+                    "how": "dvbm_probe_fp64_fma: 8 independent FMA chains x 4096 per thread, 8 x 256 threads per SM, "
+                           "best of 5 launches, CUDA events"}
+    except OSError:
+        pass
+    return None
 
 
 def run_reference(args, rank, world):
@@ -224,8 +298,11 @@ def adjoint_ratio(dvbm, inputs, torch, N=512, nsteps=200):
     """Adjoint workload: N^2 periodic FP64, multimode rms Ma 0.3 (seed 0),
     Pr 0.71, gamma 1.4, mu 1e-3, nsteps steps, loss 1/(2N^2) sum[(rho - rho_t)^2
     + (T - T_t)^2] against the same flow from seed 1 after nsteps steps;
-    checkpoints every ceil(sqrt(nsteps)).  Returns the time of the recorded
-    forward run and of dvbm_adjoint (segment recompute + adjoint steps)."""
+    checkpoints every ceil(sqrt(nsteps)).  ``ratio`` = the time of
+    dvbm_adjoint (segment recompute + adjoint steps) over nsteps plain forward
+    steps (CUDA events on an unrecorded context, after warm-up); the recorded
+    forward run (init, checkpoint copies, moments to the host) is timed beside
+    it."""
     import math as _m
     every = int(_m.ceil(_m.sqrt(nsteps)))
     tgt = inputs.multimode(N, seed=1, rms_Ma=0.3)
@@ -237,6 +314,13 @@ def adjoint_ratio(dvbm, inputs, torch, N=512, nsteps=200):
     st.close()
     F = inputs.multimode(N, seed=0, rms_Ma=0.3)
     fields = [torch.tensor(a, device="cuda") for a in (F.rho, F.ux, F.uy, F.T)]
+    # plain forward steps: the denominator of the ratio
+    plain = dvbm.Simulation(N, N, 0.71, 1.4, 1e-3, check_every=-1, dt=dt)
+    plain.init(*fields)
+    plain.step(5)
+    torch.cuda.synchronize()
+    fwd_ms, _ = timed_steps(plain, nsteps, torch.cuda.current_stream())
+    plain.close()
     out = {}
     for rep in range(2):  # first repetition warms up allocations
         sim = dvbm.Simulation(N, N, 0.71, 1.4, 1e-3, check_every=-1, dt=dt)
@@ -255,8 +339,11 @@ def adjoint_ratio(dvbm, inputs, torch, N=512, nsteps=200):
         sim.close()
         out = {"workload": f"adjoint {N}x{N} periodic multimode rms Ma 0.3, {nsteps} FP64 steps, "
                            f"checkpoints every {every}",
-               "t_forward_ms": (t1 - t0) * 1e3, "t_adjoint_ms": (t2 - t1) * 1e3,
-               "ratio": (t2 - t1) / (t1 - t0),
+               "t_forward_steps_ms": fwd_ms, "t_adjoint_ms": (t2 - t1) * 1e3,
+               "ratio": (t2 - t1) * 1e3 / fwd_ms,
+               "what": "t_adjoint / t_forward_steps: dvbm_adjoint (recompute + adjoint steps, wall clock) over "
+                       "the same number of plain forward steps (CUDA events)",
+               "t_recorded_forward_ms": (t1 - t0) * 1e3, "ratio_to_recorded_forward": (t2 - t1) / (t1 - t0),
                "grad_norms": {k: float(g[k].norm()) for k in ("rho0", "ux0", "uy0", "T0")},
                "dL_dparams": [g["mu"], g["Pr"], g["gamma"]]}
     return out
@@ -316,6 +403,8 @@ def main():
     args = parse()
     if args.sweep:
         return run_sweep(args)
+    if args.cpu_table:
+        return cpu_table()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -427,34 +516,38 @@ def main():
         return
     r64 = results["fp64"]
     # dominant kernel: the FP64 step; HBM roofline of its algorithmic bytes
+    # (800 B per cell update: 50 populations read and written)
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     ach_gbs = BYTES_PER_CELL["fp64"] * N * N / (r64["kernel_ms"] * 1e-3) / 1e9
     tr = profile_traffic("k_step_fp64")
+    roofline = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach_gbs / hbm_peak, "frac_of_8tbs": ach_gbs / NOMINAL_HBM_GBS,
+                "traffic": (tr["dram_bytes_per_cell"] * N * N if tr else None),
+                "kernel": "k_step<double> (FP64 storage, D2Q25 split II)",
+                "what": "algorithmic 800 B per cell update x cells / step-kernel time (CUDA events); peak = "
+                        + ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peak_kind == "measured"
+                           else "fallback 6.8 TB/s (of fallback)")}
+    # the second ceiling on GB300: the FP64 pipe, against the measured FMA peak
+    probe = fp64_probe()
     fp64_ops = tr.get("fp64_flops_per_cell") if tr else None
-    roofline_hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": ach_gbs / hbm_peak, "frac_of_8tbs": ach_gbs / NOMINAL_HBM_GBS,
-                    "traffic": (tr["dram_bytes_per_cell"] * N * N if tr else None),
-                    "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    roofline_fp64 = {"bound": "fp64", "unit": "TFLOP/s", "peak": probe["tflops"] if probe else NOMINAL_FP64_TFLOPS,
+                     "peak_kind": "measured (dvbm_probe_fp64_fma)" if probe else "nominal (152 SMs x 2 x 2.07 GHz x 2)",
+                     "probe": probe, "achieved": None, "frac": None}
     if fp64_ops:
         ach_tf = fp64_ops * N * N / (r64["kernel_ms"] * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": ach_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach_tf / NOMINAL_FP64_TFLOPS, "traffic": roofline_hbm["traffic"],
-                    "what": "FP64 pipe: executed FP64 flops per cell (ncu instruction mix, FMA = 2) / step-kernel time; "
-                            "peak = 152 SMs x 2 FP64 inst/clk x 2.07 GHz x 2"}
+        roofline_fp64.update({"achieved": ach_tf, "frac": ach_tf / roofline_fp64["peak"],
+                              "what": "executed FP64 flops per cell (ncu instruction mix of the profiled sources, "
+                                      "FMA = 2) x cells / step-kernel time"})
         if tr.get("thread_inst_per_cell"):
-            # the step also runs its advection and Grad expansion on the integer
-            # pipe, so the issue slots are the second ceiling
             ach_is = tr["thread_inst_per_cell"] / 32.0 * N * N / (r64["kernel_ms"] * 1e-3) / 1e9
-            roofline["issue"] = {"achieved": ach_is, "peak": NOMINAL_ISSUE_GWARPINST,
-                                 "unit": "G warp-instructions/s", "frac": ach_is / NOMINAL_ISSUE_GWARPINST,
-                                 "what": "all executed instructions (ncu) per cell / 32 x cells / step-kernel time; "
-                                         "peak = 152 SMs x 4 schedulers x 2.07 GHz"}
-    else:
-        roofline = dict(roofline_hbm)
+            roofline_fp64["issue"] = {"achieved": ach_is, "peak": NOMINAL_ISSUE_GWARPINST,
+                                      "unit": "G warp-instructions/s", "frac": ach_is / NOMINAL_ISSUE_GWARPINST,
+                                      "what": "all executed instructions (ncu) per cell / 32 x cells / step-kernel "
+                                              "time; peak = 152 SMs x 4 schedulers x 2.07 GHz"}
     line = {"metric": "MLUPS", "value": r64["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(N),
-            "roofline": roofline, "roofline_hbm": roofline_hbm, "clocks": clocks,
+            "roofline": roofline, "roofline_fp64": roofline_fp64, "clocks": clocks,
             "gpu_launches": 2 * args.steps,
             "kernel_ms_per_step": r64["kernel_ms"], "conservation_drift": r64["drift"]}
     if "fp32dev" in results:

@@ -207,20 +207,21 @@ const char* dvbm_last_error(const dvbm_ctx* ctx);
 void dvbm_destroy(dvbm_ctx* ctx);
 
 /* Allocation-free CFL time step (the paper has no counterpart: this is a
- * service for callers that cannot allocate device memory, e.g. code running
- * during CUDA graph capture, inside a framework that owns the whole device
- * memory budget, or in loops where cudaMalloc/cudaFree would synchronise).
+ * service for callers that cannot allocate device memory, e.g. code inside a
+ * framework whose caching allocator owns the whole device memory budget, or
+ * loops where cudaMalloc/cudaFree would synchronise the device).
  * Computes dt = cfl * h / max over cells of (|u| + sqrt(gamma R T)) -- the rule
  * dvbm_init applies with h = min(dx, dy) -- from n device-resident doubles
  * per field, on `stream` (a cudaStream_t or NULL), and stores dt in the host
- * double *dt_out; the call synchronises the stream.  No context, no
- * allocation: partial maxima go to a fixed 64 KiB device array inside the
- * library, held by every GPU that loads it until the process exits.  Calls
- * that overlap on the GPU share that array and race: serialise them.  The
- * first call on a device looks up the array's device address; make it before
- * any stream capture.  Errors: EINVAL (null pointer, n <= 0 or
- * n > DVBM_NOALLOC_MAX_CELLS, bad gamma/R/cfl/h, or a field with rho <= 0,
- * T <= 0 or non-finite values), ECUDA. */
+ * double *dt_out.  The call waits for the stream before it returns, for at
+ * most 600 s (the library's default time limit; DVBM_ETIMEOUT beyond it, the
+ * queued work staying queued).  No context, no device allocation: partial
+ * maxima go to a fixed 64 KiB device array inside the library, held by every
+ * GPU that loads it until the process exits.  Calls that overlap on the GPU
+ * share that array and race: serialise them.  The first call on a device
+ * looks up the array's device address.  Errors: EINVAL (null pointer,
+ * n <= 0 or n > DVBM_NOALLOC_MAX_CELLS, bad gamma/R/cfl/h, or a field with
+ * rho <= 0, T <= 0 or non-finite values), ETIMEOUT, ECUDA. */
 #define DVBM_NOALLOC_MAX_CELLS 67108864LL
 dvbm_status dvbm_cfl_dt_noalloc(const double* rho, const double* ux, const double* uy, const double* T,
                                 long long n, double gamma, double R, double cfl, double h, void* stream,

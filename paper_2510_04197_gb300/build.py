@@ -1,7 +1,8 @@
 """Build libdvbm.so in-tree with nvcc for sm_103a (no cmake, no torch extension).
 
 The translation units compile in parallel; the shared library lands next to
-this file.  Usage: ``python -m paper_2510_04197_gb300.build`` or ``build()``.
+this file, with libdvbm_probe.so (the FP64 throughput probe bench.py uses).
+Usage: ``python -m paper_2510_04197_gb300.build`` or ``build()``.
 """
 from __future__ import annotations
 
@@ -14,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdvbm.so")
 SOURCES = ["dvbm_step.cu", "dvbm_aux.cu", "dvbm_api.cu", "dvbm_noalloc.cu", "dvbm_adjoint.cu", "dvbm_d2q16.cu"]
+# the FP64 throughput probe bench.py reports the step's FP64 work against
+PROBE_SOURCE, PROBE_OUT = "dvbm_probe.cu", os.path.join(HERE, "libdvbm_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -41,8 +44,14 @@ def _compile(src: str, builddir: str, verbose: bool) -> str:
 def build(verbose: bool = False) -> str:
     builddir = os.path.join(HERE, "_build")
     os.makedirs(builddir, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, builddir, verbose), SOURCES))
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(lambda s: _compile(s, builddir, verbose), SOURCES + [PROBE_SOURCE]))
+    probe_obj = objs.pop()
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", PROBE_OUT + ".tmp", probe_obj, "-lcudart"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of the probe failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(PROBE_OUT + ".tmp", PROBE_OUT)
     tmp = OUT + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -2,12 +2,14 @@
 //
 // dvbm_cfl_dt_noalloc() computes the same CFL time step as dvbm_init,
 //   dt = cfl * h / max(|u| + sqrt(gamma R T)),
-// for callers that cannot allocate device memory: code running while a CUDA
-// stream is being captured into a graph (an allocation there breaks or
-// serialises the capture), code inside a framework that owns a fixed device
-// memory budget, and latency-critical loops where cudaMalloc / cudaFree would
-// synchronise the device.  It creates no context and allocates nothing; the
-// caller passes the four field arrays and receives dt on the host.
+// for callers that cannot allocate device memory: code inside a framework
+// that owns a fixed device memory budget (a caching allocator that has
+// reserved the device's memory, where a cudaMalloc of our own would fail or
+// evict), and latency-critical loops where cudaMalloc / cudaFree would
+// synchronise the device.  It creates no context and allocates no device
+// memory; the caller passes the four field arrays and receives dt on the
+// host.  The call waits for its stream (under a host-side time limit of
+// kWaitLimitSeconds, the library's default limit) before it returns.
 //
 // Its per-block partial maxima live in a file-scope device array of fixed
 // size (4096 blocks of 256 threads x 64 cells, 64 KiB), which every GPU that loads the
@@ -16,10 +18,11 @@
 // and must be serialised by the caller.  Each call writes every slot it reads
 // before reading it, so the contents left by an earlier call never leak into
 // a result.  The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress) once for that device; make that first call before
-// any stream capture begins.
+// (cudaGetSymbolAddress) once for that device.
+#include <chrono>
 #include <cmath>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/dvbm.h"
@@ -30,6 +33,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kCellsPerThread = 64;
 constexpr int kMaxBlocks = 4096;
+constexpr double kWaitLimitSeconds = 600.0;
 constexpr long long kMaxCells = (long long)kMaxBlocks * kThreads * kCellsPerThread;
 static_assert(kMaxCells == DVBM_NOALLOC_MAX_CELLS, "scratch size and the published maximum must agree");
 
@@ -94,6 +98,21 @@ cudaError_t scratch_for_current_device(double** out) {
   return cudaSuccess;
 }
 
+// Poll the stream until it has run everything queued on it, for at most
+// kWaitLimitSeconds: DVBM_OK, DVBM_ETIMEOUT (the work stays queued), or
+// DVBM_ECUDA for an error the stream reported.
+dvbm_status wait_idle(cudaStream_t st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int spins = 0;; ++spins) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return DVBM_OK;
+    if (e != cudaErrorNotReady) return DVBM_ECUDA;
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kWaitLimitSeconds)
+      return DVBM_ETIMEOUT;
+    if (spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
 }  // namespace
 
 extern "C" dvbm_status dvbm_cfl_dt_noalloc(const double* rho, const double* ux, const double* uy, const double* T,
@@ -108,10 +127,15 @@ extern "C" dvbm_status dvbm_cfl_dt_noalloc(const double* rho, const double* ux, 
   cudaStream_t st = (cudaStream_t)stream;
   k_speed_static<<<blocks, kThreads, 0, st>>>(rho, ux, uy, T, n, gamma * R, scratch);
   if (cudaGetLastError() != cudaSuccess) return DVBM_ECUDA;
-  double host[2 * kMaxBlocks];
-  if (cudaMemcpyAsync(host, scratch, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  // the partial maxima are read only once the stream has run the kernel: wait
+  // for it under the time limit (a copy into pageable host memory would block
+  // the calling thread for as long as the stream takes)
+  if (wait_idle(st) != DVBM_OK) return DVBM_ETIMEOUT;
+  std::vector<double> host(2 * (size_t)blocks);  // host memory only
+  if (cudaMemcpyAsync(host.data(), scratch, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return DVBM_ECUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return DVBM_ECUDA;
+  const dvbm_status w = wait_idle(st);
+  if (w != DVBM_OK) return w;
   double vmax = 0.0, bad = 0.0;
   for (int b = 0; b < blocks; ++b) {
     vmax = std::fmax(vmax, host[2 * b]);

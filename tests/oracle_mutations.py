@@ -26,6 +26,8 @@ MUTATIONS = [
     "downwind_faces",             # faces reconstructed from the downwind side
     "prandtl_branch_ignored",     # Pr > 1 relaxed with the Pr < 1 mapping of tau1, tau2
     "d2q16_weights_swapped",      # D2Q16 inner and outer 1-D weights exchanged
+    "cfl_speed_at_reference_temperature",  # c_s = sqrt(gamma R T_ref) in the time-step rule
+    "cfl_separate_maxima",        # max |u| + max c_s taken over different cells
 ]
 
 
@@ -134,6 +136,17 @@ def _apply(O, name):
                 self.w1 = w1
                 self.w = torch.tensor([w1[p] * w1[q] for p in range(4) for q in range(4)], dtype=O.DT)
         O.Lattice.__init__ = init
+    elif name == "cfl_speed_at_reference_temperature":
+        def cfl_ref(P, grid, ux, uy, T, cfl):
+            speed = torch.sqrt(ux * ux + uy * uy) + (float(P.gamma) * P.R * P.T_ref) ** 0.5
+            return cfl * min(grid.dx, grid.dy) / float(speed.max())
+        O.cfl_dt = cfl_ref
+    elif name == "cfl_separate_maxima":
+        def cfl_sep(P, grid, ux, uy, T, cfl):
+            umax = float(torch.sqrt(ux * ux + uy * uy).max())
+            cmax = float(torch.sqrt(float(P.gamma) * P.R * T).max())
+            return cfl * min(grid.dx, grid.dy) / (umax + cmax)
+        O.cfl_dt = cfl_sep
     else:
         raise ValueError(f"unknown mutation {name}")
 

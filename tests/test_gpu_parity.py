@@ -46,6 +46,34 @@ def test_config1_wave_decay_fp64_1000_steps(D):
     assert max(e.values()) < 1e-12, e
 
 
+def deviation_errors(gpu, ora):
+    """Max-norm errors per field relative to the field's largest deviation
+    from its own mean (rho, each velocity component, T): the dynamic part of
+    the flow, not its mean state, sets the scale."""
+    e = {}
+    for k in ("rho", "ux", "uy", "T"):
+        o = np.asarray(ora[k])
+        e[k] = np.abs(np.asarray(gpu[k]) - o).max() / np.abs(o - o.mean()).max()
+    return e
+
+
+@pytest.mark.parametrize("Pr", [0.71, 2.0])
+def test_large_amplitude_64_squared_1000_steps(D, Pr):
+    """O(0.1) density and temperature perturbations over a Ma 0.5 flow, 64^2,
+    1000 steps (t = 0.2, about a quarter of a viscous time of the largest
+    mode): errors relative to each field's largest deviation from its mean
+    at most 1e-10.  The bound: a step rounds each population at about 1e-16
+    of its value; over 1000 steps that grows to ~1e-13 of the mean state,
+    i.e. ~1e-12 of a deviation of 0.1, with two orders of margin."""
+    F = I.random_smooth(64, 64, seed=21, amp=0.1, Ma=0.5)
+    sim, g = gpu_run(D, F, Pr, 1.4, 2e-3, 1000, dt=2e-4)
+    _, o = oracle_run(F, Pr, 1.4, 2e-3, sim.dt, 1000)
+    e = deviation_errors(g, o)
+    assert max(e.values()) < 1e-10, e
+    # the run is far from the linear regime: the fields changed by O(amp)
+    assert np.abs(o["rho"] - F.rho).max() > 1e-2
+
+
 @pytest.mark.parametrize("Pr", [0.5, 1.0, 2.0])
 @pytest.mark.parametrize("shape", [(40, 24), (37, 13)])
 def test_ragged_grids_all_prandtl_cases(D, Pr, shape):

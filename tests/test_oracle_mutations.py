@@ -13,7 +13,7 @@ from oracle_mutations import MUTATIONS
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 # fastest files first: each child stops at its first failure
-PINS = ["test_oracle_boundaries.py", "test_oracle_pins.py", "test_oracle_split1.py", "test_oracle_physics.py"]
+PINS = ["test_oracle_cfl.py", "test_oracle_boundaries.py", "test_oracle_pins.py", "test_oracle_split1.py", "test_oracle_physics.py"]
 
 
 def run_pins(mutation):

@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-d2q16", action="store_true")
     ap.add_argument("--no-workloads", action="store_true")
+    ap.add_argument("--layout", default="slabs", choices=["slabs", "replicas"],
+                    help="with several GPUs: one band of a y-decomposed grid per GPU, halo rows over NCCL (slabs), "
+                         "or one independent grid per GPU (replicas)")
     ap.add_argument("--cpu-table", action="store_true",
                     help="the oracle's CPU baseline table on one and on all host threads (one JSON line)")
     ap.add_argument("--sweep", action="store_true",
@@ -62,11 +65,16 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(N):
+def workload_config(N, world=1, layout="slabs"):
+    if world > 1 and layout == "slabs":
+        par = (f"slabs along y: one {N}-row band per GPU of a periodic {N}x{N * world} grid (the {N}x{N} flow "
+               f"repeated in y), two halo rows per side per step over NCCL send/recv, dt and totals all-reduced")
+    else:
+        par = "replicas (one independent grid per GPU)"
     return {"workload": f"periodic multimode flow {N}x{N}, rms Ma 0.3, seed 0 (throughput sweep)",
             "grid": [N, N], "lattice": "D2Q25", "energy_split": "II", "Pr": 0.71, "gamma": 1.4, "mu": 5e-5,
             "cfl": 0.01, "beta": 1.2, "l2": "state 2x50 planes x N^2 (> 129 MB L2): no flush needed",
-            "parallelism": "replicas (one independent grid per GPU)"}
+            "parallelism": par}
 
 
 STEP_KERNEL_SOURCES = ("dvbm_device.cuh", "dvbm_step.cu")
@@ -289,7 +297,7 @@ def run_reference(args, rank, world):
     line = {"metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus, "steps": steps,
             "warmup": args.warmup, "ms_per_step": N * N / cb["value"] / 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.size), "impl": "reference", "cpu_baseline": cb,
+            "config": workload_config(args.size, world, args.layout), "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -426,7 +434,9 @@ def main():
             dist.barrier()
 
     N = args.size
-    F = inputs.multimode(N, seed=rank, rms_Ma=0.3)
+    slabs = world > 1 and args.layout == "slabs"
+    # slabs: every band holds the same flow, so the y-periodic global field is continuous across bands
+    F = inputs.multimode(N, seed=0 if slabs else rank, rms_Ma=0.3)
     fields = [torch.tensor(a) for a in (F.rho, F.ux, F.uy, F.T)]
     stream = torch.cuda.current_stream()
     peaks, peak_kind = load_peaks()
@@ -434,8 +444,13 @@ def main():
     clocks = None
     variants = ["fp64"] + ([] if args.no_fp32dev else ["fp32dev"]) + ([] if args.no_d2q16 else ["d2q16"])
     for storage in variants:
-        sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, storage=1 if storage == "fp32dev" else 0, check_every=-1,
-                              lattice=dvbm.D2Q16_SPLIT_I if storage == "d2q16" else dvbm.D2Q25_SPLIT_II)
+        kw = dict(storage=1 if storage == "fp32dev" else 0, check_every=-1,
+                  lattice=dvbm.D2Q16_SPLIT_I if storage == "d2q16" else dvbm.D2Q25_SPLIT_II)
+        if slabs:
+            from paper_2510_04197_gb300 import slab as SL
+            sim = SL.RankSlab(dist, N, N, 0.71, 1.4, 5e-5, **kw)
+        else:
+            sim = dvbm.Simulation(N, N, 0.71, 1.4, 5e-5, **kw)
         sim.init(*fields)
         tot0 = sim.totals()  # outside the timed region: the conservation drift of the whole run
         sim.step(args.warmup)
@@ -546,9 +561,9 @@ def main():
                                               "time; peak = 152 SMs x 4 schedulers x 2.07 GHz"}
     line = {"metric": "MLUPS", "value": r64["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(N),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(N, world, args.layout),
             "roofline": roofline, "roofline_fp64": roofline_fp64, "clocks": clocks,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (4 if slabs else 2) * args.steps,
             "kernel_ms_per_step": r64["kernel_ms"], "conservation_drift": r64["drift"]}
     if "fp32dev" in results:
         r32 = results["fp32dev"]

@@ -70,7 +70,15 @@ typedef enum { DVBM_FP64 = 0, DVBM_FP32DEV = 1 } dvbm_storage;
  * rho_G = rho_B, u_G = 2 u_W - u_B, T_G = 2 T_W - T_B,
  * f_G = f^eq(G) + (f_B - f^eq(B)) (same for g); ghost k mirrors interior
  * cell k, k = 1, 2. */
-typedef enum { DVBM_BC_PERIODIC = 0, DVBM_BC_ZEROGRAD = 1, DVBM_BC_WALL = 2 } dvbm_bc_kind;
+typedef enum { DVBM_BC_PERIODIC = 0, DVBM_BC_ZEROGRAD = 1, DVBM_BC_WALL = 2, DVBM_BC_EXTERNAL = 3 } dvbm_bc_kind;
+/* EXTERNAL (y sides only): the context holds one band of rows of a grid
+ * decomposed along y into slabs.  The scheme's stencil reaches two cells
+ * along each axis (Sec. III.A.2, Eq. finalDiscretePDE), so before every step
+ * the two ghost rows of an EXTERNAL side must be supplied with
+ * dvbm_halo_unpack: the neighbouring slab's two boundary rows of the same
+ * time level, taken from it with dvbm_halo_pack.  dvbm_step then advances one
+ * step per call (n <= 1) and refuses (ESTATE) while a halo is stale.  An
+ * EXTERNAL side counts as non-periodic for the pairing rule. */
 
 typedef struct {
   int kind;         /* dvbm_bc_kind */
@@ -192,6 +200,33 @@ dvbm_status dvbm_record(dvbm_ctx* ctx, int every);
  * Errors: ESTATE (no recording), EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
 dvbm_status dvbm_adjoint(dvbm_ctx* ctx, const double* dL_drho, const double* dL_dT, double* g_rho0,
                          double* g_ux0, double* g_uy0, double* g_T0, double g_params[3]);
+
+/* Slab decomposition along y (multi-GPU, Sec. III.A.1; see DVBM_BC_EXTERNAL).
+ * A halo buffer holds two rows of every population plane, layout
+ * [npop][2][Nx] of the storage type (double for FP64, float deviations for
+ * FP32DEV), rows in increasing y; dvbm_halo_bytes gives its size
+ * (2 Nx npop element bytes).
+ * dvbm_halo_pack writes the current state's two lowest interior rows
+ * (y = 0, 1) to lo and its two highest (y = Ny - 2, Ny - 1) to hi: what the
+ * lower and the upper neighbour need.  dvbm_halo_unpack writes lo into the
+ * ghost rows below the band (y = -2, -1) and hi into those above it
+ * (y = Ny, Ny + 1); every EXTERNAL side needs its buffer (else EINVAL), other
+ * sides take NULL.  Pointers are device pointers on the context's device; the
+ * copies are kernels on the context's stream (stream-ordered, no host wait).
+ * Either pointer of dvbm_halo_pack may be NULL to skip that side.
+ * Errors: EINVAL (null context, missing or unexpected buffer), ESTATE (no
+ * state yet), ECUDA. */
+size_t dvbm_halo_bytes(const dvbm_ctx* ctx);
+dvbm_status dvbm_halo_pack(dvbm_ctx* ctx, void* lo, void* hi);
+dvbm_status dvbm_halo_unpack(dvbm_ctx* ctx, const void* lo, const void* hi);
+
+/* Replace the time step fixed at dvbm_init (or dvbm_set_state) by dt, e.g.
+ * the smallest of the slabs' CFL steps so that every slab of a decomposed
+ * grid steps with the same dt (Sec. III.A.3).  dt is checked against the
+ * limits dvbm_init applies (one cell per step; the shortest relaxation time
+ * of the field given to dvbm_init).  Errors: EINVAL (dt <= 0, non-finite or
+ * beyond the limits; the time step stays as it was), ESTATE (no state yet). */
+dvbm_status dvbm_set_dt(dvbm_ctx* ctx, double dt);
 
 /* Time step size fixed at dvbm_init (0 before). */
 double dvbm_dt(const dvbm_ctx* ctx);

@@ -47,7 +47,13 @@ struct dvbm_ctx {
   double* stage = nullptr;             // 4 Nx Ny doubles staging host fields (allocated on first use)
   std::vector<void*> in_flight;        // temporaries of calls that timed out, freed by dvbm_destroy
   size_t state_bytes_dev = 0;
+  // slab decomposition along y: sides whose ghost rows come from dvbm_halo_unpack
+  bool external[2] = {false, false};  // ylo, yhi
+  bool halo_fresh = false;             // the external ghost rows hold the current time level
+  double pmax = 0.0;                   // largest pressure of the dvbm_init field (relaxation limit of dt)
 };
+
+static bool has_external(const dvbm_ctx* c) { return c->external[0] || c->external[1]; }
 
 static std::string g_create_error;
 
@@ -160,7 +166,9 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
   for (int s = 0; s < 4; ++s) {
     if (bcs) b[s] = bcs[s];
     else { b[s].kind = DVBM_BC_PERIODIC; b[s].u_wall[0] = b[s].u_wall[1] = 0; b[s].T_wall = 1; }
-    if (b[s].kind < 0 || b[s].kind > 2) return fail(nullptr, DVBM_EINVAL, "bad boundary kind on side %d", s);
+    if (b[s].kind < 0 || b[s].kind > 3) return fail(nullptr, DVBM_EINVAL, "bad boundary kind on side %d", s);
+    if (b[s].kind == DVBM_BC_EXTERNAL && s < 2)
+      return fail(nullptr, DVBM_EINVAL, "external halo rows are supported on the y sides only (slabs along y)");
     if (b[s].kind == DVBM_BC_WALL && !(b[s].T_wall > 0)) return fail(nullptr, DVBM_EINVAL, "wall T must be > 0");
   }
   for (int a = 0; a < 2; ++a)
@@ -174,6 +182,8 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
   c->Pr = Pr; c->gamma = gamma; c->mu = mu;
   c->opts = o;
   for (int s = 0; s < 4; ++s) c->bcs[s] = b[s];
+  c->external[0] = b[DVBM_YLO].kind == DVBM_BC_EXTERNAL;
+  c->external[1] = b[DVBM_YHI].kind == DVBM_BC_EXTERNAL;
   c->stream = (cudaStream_t)stream;
   const cudaError_t ed = cudaGetDevice(&c->device);
   if (ed != cudaSuccess) {
@@ -410,8 +420,10 @@ extern "C" dvbm_status dvbm_init(dvbm_ctx* c, const double* rho, const double* u
   s = check_dt(c, dt, pmax);  // before any change to the context
   if (s != DVBM_OK) return s;
   c->dt = dt;
+  c->pmax = pmax;
   set_step_factors(c);
   c->cur = 0;
+  c->halo_fresh = false;
   CUDA_TRY(c, l_init(c, c->buf[0], F.p));
   s = fill_ghosts(c, c->buf[0]);
   if (s != DVBM_OK) return s;
@@ -438,6 +450,10 @@ extern "C" dvbm_status dvbm_step(dvbm_ctx* c, int n) {
   if (!c) return DVBM_EINVAL;
   if (!c->initialised) return fail(c, DVBM_ESTATE, "dvbm_step before dvbm_init / dvbm_set_state");
   if (n < 0) return fail(c, DVBM_EINVAL, "n must be >= 0");
+  if (has_external(c) && n > 1)
+    return fail(c, DVBM_EINVAL, "a context with external halo rows advances one step per halo exchange (n <= 1)");
+  if (has_external(c) && n == 1 && !c->halo_fresh)
+    return fail(c, DVBM_ESTATE, "the external halo rows are stale: call dvbm_halo_unpack before each step");
   const int every = c->opts.check_every;
   for (int i = 0; i < n; ++i) {
     void* src = c->buf[c->cur];
@@ -447,6 +463,7 @@ extern "C" dvbm_status dvbm_step(dvbm_ctx* c, int n) {
     if (s != DVBM_OK) return s;
     c->cur = 1 - c->cur;
     ++c->steps;
+    c->halo_fresh = false;
     if (c->recorded && c->steps % c->record_every == 0) {
       s = push_checkpoint(c);
       if (s != DVBM_OK) return s;
@@ -558,7 +575,47 @@ extern "C" dvbm_status dvbm_set_state(dvbm_ctx* c, const void* buf, size_t bytes
   if (s != DVBM_OK) return s;
   c->steps = st;
   c->initialised = true;
+  c->halo_fresh = false;
   clear_record(c);
+  return DVBM_OK;
+}
+
+extern "C" size_t dvbm_halo_bytes(const dvbm_ctx* c) {
+  if (!c) return 0;
+  return (size_t)2 * c->Nx * c->npop * c->elem;
+}
+
+extern "C" dvbm_status dvbm_halo_pack(dvbm_ctx* c, void* lo, void* hi) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
+  if (!lo && !hi) return DVBM_OK;
+  CUDA_TRY(c, launch_halo(c->storage == DVBM_FP64 ? 8 : 4, c->buf[c->cur], lo, hi, 0, c->G, c->npop, c->stream));
+  return DVBM_OK;
+}
+
+extern "C" dvbm_status dvbm_halo_unpack(dvbm_ctx* c, const void* lo, const void* hi) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
+  const void* in[2] = {lo, hi};
+  for (int s = 0; s < 2; ++s) {
+    if (c->external[s] && !in[s]) return fail(c, DVBM_EINVAL, "side %s is external: its halo buffer is required", s ? "yhi" : "ylo");
+    if (!c->external[s] && in[s]) return fail(c, DVBM_EINVAL, "side %s is not external: pass NULL", s ? "yhi" : "ylo");
+  }
+  if (lo || hi)
+    CUDA_TRY(c, launch_halo(c->storage == DVBM_FP64 ? 8 : 4, c->buf[c->cur], (void*)lo, (void*)hi, 1, c->G,
+                            c->npop, c->stream));
+  c->halo_fresh = true;
+  return DVBM_OK;
+}
+
+extern "C" dvbm_status dvbm_set_dt(dvbm_ctx* c, double dt) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(c, DVBM_EINVAL, "dt must be > 0 and finite");
+  const dvbm_status s = check_dt(c, dt, c->pmax);
+  if (s != DVBM_OK) return s;
+  c->dt = dt;
+  set_step_factors(c);
   return DVBM_OK;
 }
 

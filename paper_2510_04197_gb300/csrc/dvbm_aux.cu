@@ -1,6 +1,7 @@
 // dvbm_aux.cu -- initial conditions, ghost layers, diagnostics.
 //
-//  k_init     equilibrium populations of given (rho, u, T) fields (Sec. III.A.3)
+//  k_init     equilibrium populations of given (rho, u, T) fields (Sec. III.A.3),
+//             by the step kernel's block-fixed-point Grad expansion
 //  k_ghost    two ghost layers per non-... side: periodic wrap, zero-gradient copy,
 //             or no-slip isothermal wall by ghost node + non-equilibrium
 //             extrapolation (Sec. III.E): rho_G = rho_B, u_G = 2 u_W - u_B,
@@ -52,7 +53,7 @@ __global__ void k_init(S* __restrict__ dst, const double* __restrict__ rho, cons
   if (x >= G.Nx || y >= G.Ny) return;
   const long long i = (long long)y * G.Nx + x;
   const Coeffs C = equilibrium_coeffs(rho[i], ux[i] / M.c, uy[i] / M.c, T[i] / M.T_ref, P);
-  write_expansion<S>(dst + cell_index(G, y, x), G.plane, C, P, nullptr, nullptr);
+  write_equilibrium_fix<S>(dst + cell_index(G, y, x), G.plane, C, P);
 }
 
 // one thread per (side, layer k, position along the side, population);
@@ -64,6 +65,7 @@ __global__ void k_ghost(S* __restrict__ buf, Geom G, Phys P, Macro M, BCDev bc) 
   const int side = blockIdx.y;
   const int kind = bc.kind[side];
   const int pop = blockIdx.z;
+  if (kind == 3) return;  // external: the caller supplies these rows (dvbm_halo_unpack)
   if (kind == 2 && pop != 0) return;
   const int len = side < 2 ? G.Ny : G.Nx;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,7 +209,31 @@ __global__ void k_pack(S* buf, S* packed, int to_packed, Geom G) {
   else buf[bi] = packed[pi];
 }
 
+// halo rows of a slab (one thread per element): blockIdx.y = 2 side + row,
+// blockIdx.z = population plane
+template <class S>
+__global__ void k_halo(S* buf, S* lo, S* hi, int unpack, Geom G) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int side = blockIdx.y >> 1, k = blockIdx.y & 1;
+  const int c = blockIdx.z;
+  S* ext = side == 0 ? lo : hi;
+  if (x >= G.Nx || !ext) return;
+  const int yb = unpack ? (side == 0 ? k - 2 : G.Ny + k) : (side == 0 ? k : G.Ny - 2 + k);
+  const long long bi = (long long)c * G.plane + cell_index(G, yb, x);
+  const long long ei = ((long long)c * 2 + k) * G.Nx + x;
+  if (unpack) buf[bi] = ext[ei];
+  else ext[ei] = buf[bi];
+}
+
 // ---------------------------------------------------------------- wrappers
+cudaError_t launch_halo(int elem, void* buf, void* lo, void* hi, int unpack, const Geom& G, int npop,
+                        cudaStream_t st) {
+  dim3 b(128), g((G.Nx + 127) / 128, 4, npop);
+  if (elem == 8) k_halo<double><<<g, b, 0, st>>>((double*)buf, (double*)lo, (double*)hi, unpack, G);
+  else k_halo<float><<<g, b, 0, st>>>((float*)buf, (float*)lo, (float*)hi, unpack, G);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(int storage, void* dst, const double* rho, const double* ux, const double* uy,
                         const double* T, const Geom& G, const Phys& P, const Macro& M, cudaStream_t st) {
   dim3 b(32, 4), g((G.Nx + 31) / 32, (G.Ny + 3) / 4);

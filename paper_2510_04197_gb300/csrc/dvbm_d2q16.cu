@@ -395,6 +395,7 @@ __global__ void k_ghost16(double* __restrict__ buf, Geom G, Phys P, Macro M, BCD
   const int side = blockIdx.y;
   const int kind = bc.kind[side];
   const int pop = blockIdx.z;
+  if (kind == 3) return;  // external: the caller supplies these rows (dvbm_halo_unpack)
   if (kind == 2 && pop != 0) return;
   const int len = side < 2 ? G.Ny : G.Nx;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;

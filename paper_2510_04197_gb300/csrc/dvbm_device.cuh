@@ -448,6 +448,23 @@ __device__ __forceinline__ void expand_q3_fix(const long long (&h)[3], long long
   t[1] = EA + OA; t[2] = EA - OA; t[3] = EB + OB; t[4] = EB - OB;
 }
 
+// h^b of x-node p (f: N = 4, g: N = 2) from fixed-point coefficients X, any
+// view with X(k) = field k in CoeffsFix order (f00, f10, f01, f20, f11, f02,
+// f30, f21, f12, f03, f40, f31, f22, f13, f04, g00, g10, g01, g20, g11, g02);
+// k0..k4 = khfix(p, 0..4) (value of h = h 2^(E - 1081 - kd(p)))
+template <class V>
+__device__ __forceinline__ void hfg_fix(const V& X, long long k0, long long k1, long long k2, long long k3,
+                                        long long k4, long long (&hf)[5], long long (&hg)[3]) {
+  hf[0] = mhk(X(0), k0) + mhk(X(1), k1) + mhk(X(3), k2) + mhk(X(6), k3) + mhk(X(10), k4);
+  hf[1] = mhk(X(2), k0) + mhk(X(4), k1) + mhk(X(7), k2) + mhk(X(11), k3);
+  hf[2] = mhk(X(5), k0) + mhk(X(8), k1) + mhk(X(12), k2);
+  hf[3] = mhk(X(9), k0) + mhk(X(13), k1);
+  hf[4] = mhk(X(14), k0);
+  hg[0] = mhk(X(15), k0) + mhk(X(16), k1) + mhk(X(18), k2);
+  hg[1] = mhk(X(17), k0) + mhk(X(19), k1);
+  hg[2] = mhk(X(20), k0);
+}
+
 // int64 -> float rounded to nearest (ties away from zero), value F 2^scale;
 // results below the normal float range flush to zero
 __device__ __forceinline__ float ll_to_float_rn(long long F, int scale) {
@@ -461,6 +478,52 @@ __device__ __forceinline__ float ll_to_float_rn(long long F, int scale) {
   const int ex = 127 + 63 - lz + scale + carry;
   if (ex <= 0) return 0.0f;
   return __uint_as_float((unsigned)min(ex, 255) << 23 | (ex >= 255 ? 0u : frac) | (F < 0 ? 0x80000000u : 0u));
+}
+
+// Populations of coefficient set C (a pure equilibrium: a1 = 0, k1 = 1) at one
+// padded offset, by the step kernel's fixed-point expansion instead of FP64
+// arithmetic: initial conditions (Sec. III.A.3) at FP64-or-better precision.
+// FP32-deviation storage: the reference populations w rho0 and w G0 carry
+// only a zeroth Hermite coefficient, so they are taken off C first and the
+// deviations come straight out of the expansion.
+struct RegView {
+  const long long* v;
+  __device__ __forceinline__ long long operator()(int k) const { return v[k]; }
+};
+template <class S, int p>
+__device__ __forceinline__ void write_node_fix(S* d, long long PL, const RegView& X, int Ef, int Eg) {
+  long long hf[5], hg[3], xf[5], xg[5];
+  hfg_fix(X, khfix(p, 0), khfix(p, 1), khfix(p, 2), khfix(p, 3), khfix(p, 4), hf, hg);
+  const int sf = renorm_fix(hf), sg = renorm_fix(hg);
+  expand_q5_fix(hf, xf);
+  expand_q3_fix(hg, xg);
+  const int scf = Ef - 1080 - sf - kd(p), scg = Eg - 1080 - sg - kd(p);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    if constexpr (sizeof(S) == 8) {
+      d[(5 * p + q) * PL] = Ef >= 100 ? ll_to_double_rn(xf[q], scf - kd(q)) : 0.0;
+      d[(25 + 5 * p + q) * PL] = Eg >= 100 ? ll_to_double_rn(xg[q], scg - kd(q)) : 0.0;
+    } else {
+      d[(5 * p + q) * PL] = Ef >= 100 ? ll_to_float_rn(xf[q], scf - kd(q)) : 0.0f;
+      d[(25 + 5 * p + q) * PL] = Eg >= 100 ? ll_to_float_rn(xg[q], scg - kd(q)) : 0.0f;
+    }
+  }
+}
+template <class S>
+__device__ __forceinline__ void write_equilibrium_fix(S* d, long long PL, Coeffs C, const Phys& P) {
+  if constexpr (sizeof(S) == 4) {
+    C.f00 -= P.fref0;
+    C.g00 -= P.gref0;
+  }
+  const CoeffsFix F = coeffs_to_fix(C);
+  const long long v[21] = {F.f00, F.f10, F.f01, F.f20, F.f11, F.f02, F.f30, F.f21, F.f12, F.f03, F.f40,
+                           F.f31, F.f22, F.f13, F.f04, F.g00, F.g10, F.g01, F.g20, F.g11, F.g02};
+  const RegView X{v};
+  write_node_fix<S, 0>(d, PL, X, F.Ef, F.Eg);
+  write_node_fix<S, 1>(d, PL, X, F.Ef, F.Eg);
+  write_node_fix<S, 2>(d, PL, X, F.Ef, F.Eg);
+  write_node_fix<S, 3>(d, PL, X, F.Ef, F.Eg);
+  write_node_fix<S, 4>(d, PL, X, F.Ef, F.Eg);
 }
 
 // float -> double by bit manipulation (exact; the hardware conversion runs on

@@ -6,7 +6,7 @@
 namespace dvbm {
 
 struct BCDev {
-  int kind[4];          // xlo, xhi, ylo, yhi (0 periodic, 1 zero-gradient, 2 wall)
+  int kind[4];          // xlo, xhi, ylo, yhi (0 periodic, 1 zero-gradient, 2 wall, 3 external: not filled here)
   double uw[4][2];      // wall velocity
   double Tw[4];         // wall temperature
 };
@@ -36,6 +36,11 @@ cudaError_t launch_totals(int storage, const void* src, double* partial, int nbl
 // out[blk*3 + {max speed, bad, max p}]
 cudaError_t launch_speed(const double* rho, const double* ux, const double* uy, const double* T, long long n,
                          double* partial, int nblocks, const Macro& M, cudaStream_t st);
+// halo rows of a slab: unpack = 0: rows y = 0, 1 -> lo and y = Ny - 2, Ny - 1 -> hi;
+// unpack = 1: lo -> ghost rows y = -2, -1 and hi -> y = Ny, Ny + 1; layout [npop][2][Nx]
+// of elem-byte elements (8: double, 4: float); a NULL buffer skips its side
+cudaError_t launch_halo(int elem, void* buf, void* lo, void* hi, int unpack, const Geom& G, int npop,
+                        cudaStream_t st);
 cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packed, const Geom& G, int npop,
                         cudaStream_t st);
 

@@ -68,14 +68,7 @@ __device__ __forceinline__ void fix_to_smem(const CoeffsFix& X, long long* b) {
 // h^b of x-node p from the shared-memory coefficients (value = h 2^(E - 1081 - kd(p)))
 __device__ __forceinline__ void hfg_fix_view(const FixView& X, long long k0, long long k1, long long k2, long long k3,
                                              long long k4, long long (&hf)[5], long long (&hg)[3]) {
-  hf[0] = mhk(X(0), k0) + mhk(X(1), k1) + mhk(X(3), k2) + mhk(X(6), k3) + mhk(X(10), k4);
-  hf[1] = mhk(X(2), k0) + mhk(X(4), k1) + mhk(X(7), k2) + mhk(X(11), k3);
-  hf[2] = mhk(X(5), k0) + mhk(X(8), k1) + mhk(X(12), k2);
-  hf[3] = mhk(X(9), k0) + mhk(X(13), k1);
-  hf[4] = mhk(X(14), k0);
-  hg[0] = mhk(X(15), k0) + mhk(X(16), k1) + mhk(X(18), k2);
-  hg[1] = mhk(X(17), k0) + mhk(X(19), k1);
-  hg[2] = mhk(X(20), k0);
+  hfg_fix(X, k0, k1, k2, k3, k4, hf, hg);
 }
 __device__ __forceinline__ void hfg_fix_view_centre(const FixView& X, long long (&hf)[5], long long (&hg)[3]) {
   constexpr long long k0 = khfix(0, 0), k2 = khfix(0, 2), k4 = khfix(0, 4);

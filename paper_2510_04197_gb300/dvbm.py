@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSTABLE", "ETIMEOUT", "ESTATE"]
 D2Q25_SPLIT_II, D2Q16_SPLIT_I = 0, 1
 FP64, FP32DEV = 0, 1
-PERIODIC, ZEROGRAD, WALL = 0, 1, 2
+PERIODIC, ZEROGRAD, WALL, EXTERNAL = 0, 1, 2, 3
 XLO, XHI, YLO, YHI = 0, 1, 2, 3
 
 
@@ -60,6 +60,10 @@ SIGNATURES = {
     "dvbm_destroy": (None, [_VP]),
     "dvbm_record": (_CI, [_VP, _CI]),
     "dvbm_adjoint": (_CI, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP]),
+    "dvbm_halo_bytes": (ctypes.c_size_t, [_VP]),
+    "dvbm_halo_pack": (_CI, [_VP, _VP, _VP]),
+    "dvbm_halo_unpack": (_CI, [_VP, _VP, _VP]),
+    "dvbm_set_dt": (_CI, [_VP, _CD]),
     "dvbm_cfl_dt_noalloc": (_CI, [_VP, _VP, _VP, _VP, ctypes.c_longlong, _CD, _CD, _CD, _CD, _VP, _DP]),
 }
 
@@ -111,6 +115,15 @@ def make_bcs(bcs: Optional[Sequence] = None):
             arr[s].kind = int(b)
             arr[s].T_wall = 1.0
     return arr
+
+
+def _ptr(t):
+    """Device pointer of a contiguous tensor, or None."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("halo buffers must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _torch():
@@ -253,6 +266,31 @@ class Simulation:
                                                              for k in ("rho0", "ux0", "uy0", "T0")], gp), self._h)
         out["mu"], out["Pr"], out["gamma"] = gp[0], gp[1], gp[2]
         return out
+
+    # -- slabs of a grid decomposed along y (EXTERNAL y sides)
+    @property
+    def halo_bytes(self) -> int:
+        return int(lib().dvbm_halo_bytes(self._h))
+
+    def halo_buffer(self):
+        """An empty device buffer for one side's halo rows, [npop, 2, Nx]."""
+        torch = _torch()
+        dt = torch.float64 if self.storage == FP64 else torch.float32
+        return torch.empty((self.npop, 2, self.Nx), dtype=dt, device=self.device)
+
+    def halo_pack(self, lo=None, hi=None):
+        """Copy the band's two lowest rows into lo and two highest into hi."""
+        _check(lib().dvbm_halo_pack(self._h, _ptr(lo), _ptr(hi)), self._h)
+        return self
+
+    def halo_unpack(self, lo=None, hi=None):
+        """Fill the ghost rows below (lo) and above (hi) the band."""
+        _check(lib().dvbm_halo_unpack(self._h, _ptr(lo), _ptr(hi)), self._h)
+        return self
+
+    def set_dt(self, dt: float):
+        _check(lib().dvbm_set_dt(self._h, float(dt)), self._h)
+        return self
 
     @property
     def dt(self) -> float:

@@ -48,7 +48,8 @@ def test_default_opts_are_paper_defaults(L):
     (dict(Pr=0.0), "Pr"), (dict(Pr=-1.0), "Pr"), (dict(gamma=1.0), "gamma"), (dict(gamma=2.5), "gamma"),
     (dict(mu=0.0), "mu"), (dict(Nx=3), "grid"), (dict(Ny=2), "grid"), (dict(storage=7), "storage"),
     (dict(lattice=3), "lattice"), (dict(bcs=[0, 1, 0, 0]), "paired"), (dict(beta=0.5), "beta"),
-    (dict(bcs=[0, 0, 5, 5]), "kind"),
+    (dict(bcs=[0, 0, 5, 5]), "kind"), (dict(bcs=[3, 3, 0, 0]), "external"), (dict(bcs=[3, 1, 0, 0]), "external"),
+    (dict(bcs=[0, 0, 3, 0]), "paired"),
 ])
 def test_create_rejects_invalid_arguments(L, args, frag):
     a = dict(lattice=0, Nx=16, Ny=16, Pr=0.71, gamma=1.4, mu=1e-3, bcs=None, storage=0, beta=1.2)
@@ -69,6 +70,10 @@ def test_null_context_calls_fail_cleanly(L):
     assert lib.dvbm_moments(None, None, None, None, None, 1) == L.EINVAL
     assert lib.dvbm_state_bytes(None) == 0
     assert lib.dvbm_dt(None) == 0.0
+    assert lib.dvbm_halo_bytes(None) == 0
+    assert lib.dvbm_halo_pack(None, None, None) == L.EINVAL
+    assert lib.dvbm_halo_unpack(None, None, None) == L.EINVAL
+    assert lib.dvbm_set_dt(None, 1e-3) == L.EINVAL
     lib.dvbm_destroy(None)
     st = lib.dvbm_create(None, 0, 16, 16, 0.71, 1.4, 1e-3, None, 0, None, None)
     assert st == L.EINVAL

@@ -1,14 +1,20 @@
-"""Slab decomposition of the step along y on CPU ranks (gloo, world size 2).
+"""Slab decomposition of the step along y on CPU ranks (gloo).
 
-Each rank owns a band of rows, exchanges two halo rows with each neighbour
-per step (point-to-point send/recv, periodic ring), and steps its band with
-the oracle.  The gathered result must be bitwise equal to the undecomposed
-run: the decomposition changes no arithmetic.  This is the exchange step a
-multi-GPU run of one grid would need; every GPU run here uses one GPU, so it
-is validated on CPU ranks."""
+Each rank owns a band of rows and exchanges two halo rows with each
+neighbour per step through ``paper_2510_04197_gb300.slab.exchange`` -- the
+same point-to-point exchange a multi-GPU run uses with NCCL -- with its halo
+buffers in the library's [npop][2][Nx] layout (f planes then g planes).  Each
+band is stepped with the oracle.  The decomposition changes no arithmetic, but
+torch's CPU kernels may round a band-shaped array differently from the full
+one, so the gathered result must equal the undecomposed run to rounding
+(1e-14 of the largest population), while halos delivered to the wrong side
+(a planted mistake) miss it by orders of magnitude.  World sizes 2 (both
+neighbours of a band are the same rank) and 3, y-periodic and zero-gradient
+in y."""
 import os
 import socket
 
+import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
@@ -27,11 +33,12 @@ def _free_port():
     return p
 
 
-def _setup(Nx, Ny):
+def _setup(Nx, Ny, periodic):
     F = I.random_smooth(Nx, Ny, seed=12, amp=0.1, Ma=0.5)
     P = O.Params(Pr=0.71, gamma=1.4, mu=2e-3)
     lat = O.Lattice()
-    grid = O.Grid(Nx, Ny, F.Lx, F.Ly)
+    ybc = O.BC() if periodic else O.BC(O.ZEROGRAD)
+    grid = O.Grid(Nx, Ny, F.Lx, F.Ly, (O.BC(), O.BC(), ybc, ybc))
     t = lambda a: torch.tensor(a, dtype=DT)
     f, g = O.init_populations(lat, P, t(F.rho), t(F.ux), t(F.uy), t(F.T))
     return lat, P, grid, f, g
@@ -53,32 +60,35 @@ class _SlabGrid(O.Grid):
         return self._dy
 
 
-def _worker(rank, world, port, Nx, Ny, nsteps, dt, out_path):
+def _worker(rank, world, port, Nx, Ny, nsteps, dt, periodic, out_path, swap=False):
+    from paper_2510_04197_gb300 import slab
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        lat, P, grid, f, g = _setup(Nx, Ny)
+        lat, P, grid, f, g = _setup(Nx, Ny, periodic)
+        Q = lat.Q
         rows = Ny // world
         y0 = rank * rows
-        slab = _SlabGrid(grid, rows)
+        band = _SlabGrid(grid, rows)
         fl, gl = f[:, y0:y0 + rows].clone(), g[:, y0:y0 + rows].clone()
-        up, down = (rank + 1) % world, (rank - 1) % world
+        lower, upper = slab.neighbours(rank, world, periodic)
+        recv_lo = torch.empty(2 * Q, 2, Nx, dtype=DT) if lower is not None else None
+        recv_hi = torch.empty(2 * Q, 2, Nx, dtype=DT) if upper is not None else None
         for _ in range(nsteps):
-            # send my two bottom rows down and two top rows up; receive halos
-            bot = torch.cat([fl[:, :2], gl[:, :2]]).contiguous()
-            top = torch.cat([fl[:, -2:], gl[:, -2:]]).contiguous()
-            from_down = torch.empty_like(top)
-            from_up = torch.empty_like(bot)
-            # tag 1: rows travelling down the ring, tag 2: rows travelling up
-            reqs = [dist.isend(bot, down, tag=1), dist.isend(top, up, tag=2),
-                    dist.irecv(from_down, down, tag=2), dist.irecv(from_up, up, tag=1)]
-            for r in reqs:
-                r.wait()
-            Q = lat.Q
-            fpy = torch.cat([from_down[:Q], fl, from_up[:Q]], dim=1)
-            gpy = torch.cat([from_down[Q:], gl, from_up[Q:]], dim=1)
-            fl, gl = O.step_with_y_halos(lat, P, slab, fl, gl, fpy, gpy, dt)
+            send_lo = torch.cat([fl[:, :2], gl[:, :2]]).contiguous()    # rows y = 0, 1
+            send_hi = torch.cat([fl[:, -2:], gl[:, -2:]]).contiguous()  # rows y = rows - 2, rows - 1
+            if swap:  # planted mistake: each band's halos land on the wrong side
+                slab.exchange(dist, rank, world, periodic, send_lo, send_hi, recv_hi, recv_lo)
+            else:
+                slab.exchange(dist, rank, world, periodic, send_lo, send_hi, recv_lo, recv_hi)
+            # ghost rows at a non-periodic domain edge come from the boundary condition
+            fb, gb = O.pad_axis(lat, P, fl, gl, 1, grid.bcs[2], grid.bcs[3])
+            below = recv_lo if recv_lo is not None else torch.cat([fb[:, :2], gb[:, :2]])
+            above = recv_hi if recv_hi is not None else torch.cat([fb[:, -2:], gb[:, -2:]])
+            fpy = torch.cat([below[:Q], fl, above[:Q]], dim=1)
+            gpy = torch.cat([below[Q:], gl, above[Q:]], dim=1)
+            fl, gl = O.step_with_y_halos(lat, P, band, fl, gl, fpy, gpy, dt)
         parts = [torch.empty_like(fl) for _ in range(world)] if rank == 0 else None
         gparts = [torch.empty_like(gl) for _ in range(world)] if rank == 0 else None
         dist.gather(fl, parts, dst=0)
@@ -89,13 +99,24 @@ def _worker(rank, world, port, Nx, Ny, nsteps, dt, out_path):
         dist.destroy_process_group()
 
 
-def test_slab_decomposition_is_bitwise_equal(tmp_path):
-    Nx, Ny, nsteps, dt = 12, 16, 5, 2e-4
-    out = str(tmp_path / "slabs.pt")
-    mp.start_processes(_worker, args=(2, _free_port(), Nx, Ny, nsteps, dt, out), nprocs=2, join=True,
-                       start_method="spawn")
+def _run(tmp_path, world, periodic, swap=False):
+    Nx, Ny, nsteps, dt = 12, 6 * world, 5, 2e-4
+    out = str(tmp_path / f"slabs{int(swap)}.pt")
+    mp.start_processes(_worker, args=(world, _free_port(), Nx, Ny, nsteps, dt, periodic, out, swap), nprocs=world,
+                       join=True, start_method="spawn")
     fd, gd = torch.load(out)
-    lat, P, grid, f, g = _setup(Nx, Ny)
+    lat, P, grid, f, g = _setup(Nx, Ny, periodic)
     for _ in range(nsteps):
         f, g = O.step(lat, P, grid, f, g, dt)
-    assert torch.equal(fd, f) and torch.equal(gd, g)
+    return float((fd - f).abs().max() / f.abs().max()), float((gd - g).abs().max() / g.abs().max())
+
+
+@pytest.mark.parametrize("world,periodic", [(2, True), (3, True), (3, False)])
+def test_slab_decomposition_matches_undecomposed_run(tmp_path, world, periodic):
+    ef, eg = _run(tmp_path, world, periodic)
+    assert ef < 1e-14 and eg < 1e-14, (ef, eg)
+
+
+def test_halos_on_the_wrong_side_are_caught(tmp_path):
+    ef, eg = _run(tmp_path, 3, True, swap=True)
+    assert ef > 1e-8 and eg > 1e-8, (ef, eg)

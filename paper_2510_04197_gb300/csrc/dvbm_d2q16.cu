@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, 
     Eg = Xr.Eg;
   }
   // x-nodes p = 0..3 in a run-time loop (one copy of the body: the kernel
-  // stays small enough for the instruction cache); the y-nodes are unrolled.
+  // stays small enough for the instruction cache).
   // The Grad expansion runs in block fixed point on the integer pipe.
 #pragma unroll 1
   for (int p = 0; p < 4; ++p) {
@@ -312,8 +312,11 @@ __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, 
     const long long pbase = (long long)(4 * p) * PL;
 #pragma unroll 1
     for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
+      double tk[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 4; ++q) tk[q] = k == 0 ? tf[q] : tg[q];
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {  // y-nodes rolled too: one copy of the population body
         const long long co = pbase + (long long)(q + 16 * k) * PL;
         const double* pc = s + co;
         double fx, fy;
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, 
           fx = flux_difference_int(pc, 1, P.hq, sx);
           fy = flux_difference_int(pc, PT, P.hq, sgn(q));
         }
-        double v = fma(C.a1, __ldg(pc), k == 0 ? tf[q] : tg[q]);
+        double v = fma(C.a1, __ldg(pc), q == 0 ? tk[0] : q == 1 ? tk[1] : q == 2 ? tk[2] : tk[3]);
         v = fma(-kx, fx, v);
         v = fma(RAT ? -P.kyr[q] : -P.kyv[q], fy, v);
         d[co] = v;

@@ -140,13 +140,20 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
   }
   const A hb = (A)P.hb;
   const long long pbase = (long long)(5 * p) * PL;
+  // FP64 storage also rolls the y-node loop (one copy of the population body:
+  // fewer instruction-cache misses, 964 -> 986 MLUPS at 4096^2, bitwise the same
+  // result); FP32-deviation storage keeps it unrolled (1754 vs 1722 MLUPS rolled)
+  constexpr bool ROLLQ = sizeof(S) == 8;
 #pragma unroll 1
   for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
+    A tk[5];
 #pragma unroll
+    for (int q = 0; q < 5; ++q) tk[q] = k == 0 ? tf[q] : tg[q];
+#pragma unroll (ROLLQ ? 1 : 5)
     for (int q = 0; q < 5; ++q) {
       const long long co = pbase + (long long)(q + 25 * k) * PL;
       const S* pc = s + co;
-      const A t = k == 0 ? tf[q] : tg[q];
+      const A t = ROLLQ ? (q == 0 ? tk[0] : q == 1 ? tk[1] : q == 2 ? tk[2] : q == 3 ? tk[3] : tk[4]) : tk[q];
       A fx = 0, fy = 0;
       if constexpr (sizeof(S) == 8) {
         if constexpr (CODES) {

@@ -305,8 +305,7 @@ static dvbm_status check_flag(dvbm_ctx* c) {
 }
 
 static dvbm_status fill_ghosts(dvbm_ctx* c, void* b) {
-  if (c->lattice == DVBM_D2Q16_SPLIT_I) CUDA_TRY(c, launch_ghost16(b, c->G, c->P, c->M, c->bc, c->stream));
-  else CUDA_TRY(c, launch_ghost(c->storage, b, c->G, c->P, c->M, c->bc, c->stream));
+  CUDA_TRY(c, launch_ghost(c->lattice, c->storage, b, c->G, c->P, c->M, c->bc, c->stream));
   return DVBM_OK;
 }
 
@@ -316,18 +315,13 @@ static cudaError_t l_step(dvbm_ctx* c, const void* src, void* dst) {
                                           : launch_step(c->storage, src, dst, c->G, c->P, c->flag, c->stream);
 }
 static cudaError_t l_init(dvbm_ctx* c, void* dst, const double* const* F) {
-  return c->lattice == DVBM_D2Q16_SPLIT_I
-             ? launch_init16(dst, F[0], F[1], F[2], F[3], c->G, c->P, c->M, c->stream)
-             : launch_init(c->storage, dst, F[0], F[1], F[2], F[3], c->G, c->P, c->M, c->stream);
+  return launch_init(c->lattice, c->storage, dst, F[0], F[1], F[2], F[3], c->G, c->P, c->M, c->stream);
 }
 static cudaError_t l_moments(dvbm_ctx* c, const void* src, double* r, double* a, double* b, double* t) {
-  return c->lattice == DVBM_D2Q16_SPLIT_I ? launch_moments16(src, r, a, b, t, c->G, c->P, c->M, c->stream)
-                                          : launch_moments(c->storage, src, r, a, b, t, c->G, c->P, c->M, c->stream);
+  return launch_moments(c->lattice, c->storage, src, r, a, b, t, c->G, c->P, c->M, c->stream);
 }
 static cudaError_t l_totals(dvbm_ctx* c, const void* src) {
-  return c->lattice == DVBM_D2Q16_SPLIT_I
-             ? launch_totals16(src, c->partial, c->nred, c->G, c->P, c->M, c->stream)
-             : launch_totals(c->storage, src, c->partial, c->nred, c->G, c->P, c->M, c->stream);
+  return launch_totals(c->lattice, c->storage, src, c->partial, c->nred, c->G, c->P, c->M, c->stream);
 }
 
 // device copies of host field arrays (or pass-through for device pointers)
@@ -685,7 +679,7 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
   e = launch_adjoint_final((const double*)c->buf[c->cur], dL_drho, dL_dT, (double*)lam[a], part + slot * nblk * 4,
                            c->G, c->P, c->M, c->stream);
   ++slot;
-  if (e == cudaSuccess) e = launch_ghost(0, lam[a], c->G, c->P, c->M, per, c->stream);
+  if (e == cudaSuccess) e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, lam[a], c->G, c->P, c->M, per, c->stream);
   const long long nseg = (n + k - 1) / k;
   for (long long j = nseg - 1; j >= 0 && e == cudaSuccess; --j) {
     const long long S = j * k, E = std::min<long long>((j + 1) * k, n);
@@ -696,7 +690,7 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
         e = launch_step_codes(seg[t], seg[t + 1], c->G, c->P, c->flag, codes + t * code_step,
                               moms ? moms + t * mom_step : nullptr, c->stream);
       else e = launch_step(0, seg[t], seg[t + 1], c->G, c->P, c->flag, c->stream);
-      if (e == cudaSuccess && t + 1 < E - S) e = launch_ghost(0, seg[t + 1], c->G, c->P, c->M, c->bc, c->stream);
+      if (e == cudaSuccess && t + 1 < E - S) e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, seg[t + 1], c->G, c->P, c->M, c->bc, c->stream);
     }
     for (long long t = E - S - 1; t >= 0 && e == cudaSuccess; --t) {
       e = launch_adjoint_step((const double*)seg[t], (const double*)lam[a], (double*)lam[1 - a],
@@ -704,7 +698,7 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
                               moms ? moms + t * mom_step : nullptr, c->G, c->P, c->stream);
       ++slot;
       a = 1 - a;
-      if (e == cudaSuccess) e = launch_ghost(0, lam[a], c->G, c->P, c->M, per, c->stream);
+      if (e == cudaSuccess) e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, lam[a], c->G, c->P, c->M, per, c->stream);
     }
   }
   const double* F0 = c->init_fields;

@@ -1,7 +1,10 @@
 // dvbm_aux.cu -- initial conditions, ghost layers, diagnostics.
 //
+// Each kernel below is written once for both models: templated on the
+// lattice traits L25 / L16 of dvbm_lattice.cuh and on the storage type.
+//
 //  k_init     equilibrium populations of given (rho, u, T) fields (Sec. III.A.3),
-//             by the step kernel's block-fixed-point Grad expansion
+//             by the step kernels' block-fixed-point Grad expansion
 //  k_ghost    two ghost layers per non-... side: periodic wrap, zero-gradient copy,
 //             or no-slip isothermal wall by ghost node + non-equilibrium
 //             extrapolation (Sec. III.E): rho_G = rho_B, u_G = 2 u_W - u_B,
@@ -12,55 +15,25 @@
 //  k_speed    per-block maxima of |u| + sqrt(gamma R T) (CFL rule) and of p = rho R T
 //             (shortest relaxation time), and a bad-input count
 //  k_pack     padded <-> packed [50][Ny][Nx] state copies
-#include "dvbm_device.cuh"
-#include "dvbm_cellmom.cuh"
-#include "dvbm_internal.h"
+#include "dvbm_lattice.cuh"
 
 namespace dvbm {
 
-// write the expansion of coefficient set C (pure equilibrium: a1 = 0, k1 = 1)
-// at one padded offset; addf/addg (nullable) add per-population values.
-template <class S>
-__device__ __forceinline__ void write_expansion(S* d, long long PL, const Coeffs& C, const Phys& P,
-                                                const double* addf, const double* addg) {
-#define DVBM_EXP(p)                                                              \
-  {                                                                              \
-    double hf[5], tf[5], hg[3], tg[5];                                           \
-    hf_of<p>(C, hf); expand_q5(hf, tf);                                          \
-    hg_of<p>(C, hg); expand_q3(hg, tg);                                          \
-    _Pragma("unroll") for (int q = 0; q < 5; ++q) {                              \
-      double vf = tf[q], vg = tg[q];                                             \
-      if (addf) { vf += addf[5 * p + q]; vg += addg[5 * p + q]; }                \
-      if constexpr (sizeof(S) == 8) {                                            \
-        d[(5 * p + q) * PL] = vf;                                                \
-        d[(25 + 5 * p + q) * PL] = vg;                                           \
-      } else {                                                                   \
-        const double w = w_of(p) * w_of(q);                                      \
-        d[(5 * p + q) * PL] = __double2float_rn(vf - P.fref0 * w);               \
-        d[(25 + 5 * p + q) * PL] = __double2float_rn(vg - P.gref0 * w);          \
-      }                                                                          \
-    }                                                                            \
-  }
-  DVBM_EXP(0) DVBM_EXP(1) DVBM_EXP(2) DVBM_EXP(3) DVBM_EXP(4)
-#undef DVBM_EXP
-}
-
-template <class S>
+template <class L, class S>
 __global__ void k_init(S* __restrict__ dst, const double* __restrict__ rho, const double* __restrict__ ux,
                        const double* __restrict__ uy, const double* __restrict__ T, Geom G, Phys P, Macro M) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= G.Nx || y >= G.Ny) return;
   const long long i = (long long)y * G.Nx + x;
-  const Coeffs C = equilibrium_coeffs(rho[i], ux[i] / M.c, uy[i] / M.c, T[i] / M.T_ref, P);
-  write_equilibrium_fix<S>(dst + cell_index(G, y, x), G.plane, C, P);
+  L::template write_equilibrium<S>(dst + cell_index(G, y, x), G.plane, rho[i], ux[i], uy[i], T[i], P, M);
 }
 
 // one thread per (side, layer k, position along the side, population);
 // sides 0..3 = xlo, xhi, ylo, yhi, blockIdx.z = population.  Periodic and
 // zero-gradient sides copy one population per thread; a wall side needs all
 // populations of its mirror cell and is done by the blockIdx.z = 0 slice.
-template <class S>
+template <class L, class S>
 __global__ void k_ghost(S* __restrict__ buf, Geom G, Phys P, Macro M, BCDev bc) {
   const int side = blockIdx.y;
   const int kind = bc.kind[side];
@@ -89,48 +62,25 @@ __global__ void k_ghost(S* __restrict__ buf, Geom G, Phys P, Macro M, BCDev bc) 
     gptr[pop * PL] = bptr[pop * PL];
     return;
   }
-  // wall: equilibrium at the ghost state + non-equilibrium part of the mirror cell
-  const Moments m = cell_moments<S>(bptr, PL, P);
-  double rho, ux, uy, T;
-  macro_from_moments(m, P, M.c, M.T_ref, rho, ux, uy, T);
-  const Coeffs CB = equilibrium_coeffs(rho, ux / M.c, uy / M.c, T / M.T_ref, P);
-  const double uxg = 2.0 * bc.uw[side][0] - ux, uyg = 2.0 * bc.uw[side][1] - uy, Tg = 2.0 * bc.Tw[side] - T;
-  const Coeffs CG = equilibrium_coeffs(rho, uxg / M.c, uyg / M.c, Tg / M.T_ref, P);
-  double neqf[25], neqg[25];
-  {
-    double hf[5], tf[5], hg[3], tg[5];
-#define DVBM_NEQ(p)                                                                    \
-    hf_of<p>(CB, hf); expand_q5(hf, tf); hg_of<p>(CB, hg); expand_q3(hg, tg);          \
-    _Pragma("unroll") for (int q = 0; q < 5; ++q) {                                    \
-      double w = 0.0;                                                                  \
-      if constexpr (sizeof(S) == 4) w = w_of(p) * w_of(q);                             \
-      neqf[5 * p + q] = ((double)bptr[(5 * p + q) * PL] + P.fref0 * w) - tf[q];        \
-      neqg[5 * p + q] = ((double)bptr[(25 + 5 * p + q) * PL] + P.gref0 * w) - tg[q];   \
-    }
-    DVBM_NEQ(0) DVBM_NEQ(1) DVBM_NEQ(2) DVBM_NEQ(3) DVBM_NEQ(4)
-#undef DVBM_NEQ
-  }
-  write_expansion<S>(gptr, PL, CG, P, neqf, neqg);
+  L::template wall_ghost<S>(gptr, bptr, PL, P, M, bc.uw[side][0], bc.uw[side][1], bc.Tw[side]);
 }
 
-template <class S>
+template <class L, class S>
 __global__ void k_moments(const S* __restrict__ src, double* rho, double* ux, double* uy, double* T, Geom G,
                           Phys P, Macro M) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= G.Nx || y >= G.Ny) return;
-  const Moments m = cell_moments<S>(src + cell_index(G, y, x), G.plane, P);
-  double r, a, b, t;
-  macro_from_moments(m, P, M.c, M.T_ref, r, a, b, t);
+  const CellState c = L::template state<S>(src + cell_index(G, y, x), G.plane, P, M);
   const long long i = (long long)y * G.Nx + x;
-  if (rho) rho[i] = r;
-  if (ux) ux[i] = a;
-  if (uy) uy[i] = b;
-  if (T) T[i] = t;
+  if (rho) rho[i] = c.rho;
+  if (ux) ux[i] = c.ux;
+  if (uy) uy[i] = c.uy;
+  if (T) T[i] = c.T;
 }
 
 // block of 256 threads; grid-stride over cells; fixed-order block reduction
-template <class S>
+template <class L, class S>
 __global__ void __launch_bounds__(256) k_totals(const S* __restrict__ src, double* partial, Geom G, Phys P,
                                                 Macro M) {
   double acc[5] = {0, 0, 0, 0, 0};
@@ -138,16 +88,12 @@ __global__ void __launch_bounds__(256) k_totals(const S* __restrict__ src, doubl
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(i / G.Nx), x = (int)(i % G.Nx);
-    const Moments m = cell_moments<S>(src + cell_index(G, y, x), G.plane, P);
-    const double rho = m.m00;
-    const double E = m.g00 + 0.5 * P.c2 * (m.m20 + m.m02);
-    double r, a, b, t;
-    macro_from_moments(m, P, M.c, M.T_ref, r, a, b, t);
-    acc[0] += rho;
-    acc[1] += m.m10 * M.c;
-    acc[2] += m.m01 * M.c;
-    acc[3] += E;
-    if (!(r > 0.0) || !(t > 0.0) || !(fabs(E) < 1e300)) acc[4] += 1.0;
+    const CellState c = L::template state<S>(src + cell_index(G, y, x), G.plane, P, M);
+    acc[0] += c.rho;
+    acc[1] += c.jx;
+    acc[2] += c.jy;
+    acc[3] += c.E;
+    if (!(c.rho > 0.0) || !(c.T > 0.0) || !(fabs(c.E) < 1e300)) acc[4] += 1.0;
   }
   __shared__ double sh[5][256];
 #pragma unroll
@@ -234,35 +180,40 @@ cudaError_t launch_halo(int elem, void* buf, void* lo, void* hi, int unpack, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_init(int storage, void* dst, const double* rho, const double* ux, const double* uy,
+// lattice 0: D2Q25 (storage 0 FP64, 1 FP32-deviation); lattice 1: D2Q16 (FP64)
+cudaError_t launch_init(int lattice, int storage, void* dst, const double* rho, const double* ux, const double* uy,
                         const double* T, const Geom& G, const Phys& P, const Macro& M, cudaStream_t st) {
   dim3 b(32, 4), g((G.Nx + 31) / 32, (G.Ny + 3) / 4);
-  if (storage == 0) k_init<double><<<g, b, 0, st>>>((double*)dst, rho, ux, uy, T, G, P, M);
-  else k_init<float><<<g, b, 0, st>>>((float*)dst, rho, ux, uy, T, G, P, M);
+  if (lattice == 1) k_init<L16, double><<<g, b, 0, st>>>((double*)dst, rho, ux, uy, T, G, P, M);
+  else if (storage == 0) k_init<L25, double><<<g, b, 0, st>>>((double*)dst, rho, ux, uy, T, G, P, M);
+  else k_init<L25, float><<<g, b, 0, st>>>((float*)dst, rho, ux, uy, T, G, P, M);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ghost(int storage, void* buf, const Geom& G, const Phys& P, const Macro& M, const BCDev& bc,
-                         cudaStream_t st) {
+cudaError_t launch_ghost(int lattice, int storage, void* buf, const Geom& G, const Phys& P, const Macro& M,
+                         const BCDev& bc, cudaStream_t st) {
   const int len = G.Nx > G.Ny ? G.Nx : G.Ny;
-  dim3 b(128), g((2 * len + 127) / 128, 4, NPOP);
-  if (storage == 0) k_ghost<double><<<g, b, 0, st>>>((double*)buf, G, P, M, bc);
-  else k_ghost<float><<<g, b, 0, st>>>((float*)buf, G, P, M, bc);
+  dim3 b(128), g((2 * len + 127) / 128, 4, lattice == 1 ? L16::NPOP : L25::NPOP);
+  if (lattice == 1) k_ghost<L16, double><<<g, b, 0, st>>>((double*)buf, G, P, M, bc);
+  else if (storage == 0) k_ghost<L25, double><<<g, b, 0, st>>>((double*)buf, G, P, M, bc);
+  else k_ghost<L25, float><<<g, b, 0, st>>>((float*)buf, G, P, M, bc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments(int storage, const void* src, double* rho, double* ux, double* uy, double* T,
+cudaError_t launch_moments(int lattice, int storage, const void* src, double* rho, double* ux, double* uy, double* T,
                            const Geom& G, const Phys& P, const Macro& M, cudaStream_t st) {
   dim3 b(32, 4), g((G.Nx + 31) / 32, (G.Ny + 3) / 4);
-  if (storage == 0) k_moments<double><<<g, b, 0, st>>>((const double*)src, rho, ux, uy, T, G, P, M);
-  else k_moments<float><<<g, b, 0, st>>>((const float*)src, rho, ux, uy, T, G, P, M);
+  if (lattice == 1) k_moments<L16, double><<<g, b, 0, st>>>((const double*)src, rho, ux, uy, T, G, P, M);
+  else if (storage == 0) k_moments<L25, double><<<g, b, 0, st>>>((const double*)src, rho, ux, uy, T, G, P, M);
+  else k_moments<L25, float><<<g, b, 0, st>>>((const float*)src, rho, ux, uy, T, G, P, M);
   return cudaGetLastError();
 }
 
-cudaError_t launch_totals(int storage, const void* src, double* partial, int nblocks, const Geom& G, const Phys& P,
-                          const Macro& M, cudaStream_t st) {
-  if (storage == 0) k_totals<double><<<nblocks, 256, 0, st>>>((const double*)src, partial, G, P, M);
-  else k_totals<float><<<nblocks, 256, 0, st>>>((const float*)src, partial, G, P, M);
+cudaError_t launch_totals(int lattice, int storage, const void* src, double* partial, int nblocks, const Geom& G,
+                          const Phys& P, const Macro& M, cudaStream_t st) {
+  if (lattice == 1) k_totals<L16, double><<<nblocks, 256, 0, st>>>((const double*)src, partial, G, P, M);
+  else if (storage == 0) k_totals<L25, double><<<nblocks, 256, 0, st>>>((const double*)src, partial, G, P, M);
+  else k_totals<L25, float><<<nblocks, 256, 0, st>>>((const float*)src, partial, G, P, M);
   return cudaGetLastError();
 }
 

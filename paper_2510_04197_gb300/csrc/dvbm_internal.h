@@ -23,14 +23,16 @@ cudaError_t launch_step(int storage, const void* src, void* dst, const Geom& G, 
 // moms[k][y][x] in Moments field order
 cudaError_t launch_step_codes(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
                               unsigned char* codes, double* moms, cudaStream_t st);
-cudaError_t launch_init(int storage, void* dst, const double* rho, const double* ux, const double* uy,
+// auxiliary kernels, written once for both models: lattice 0 = D2Q25 / split II
+// (storage 0 FP64, 1 FP32-deviation), lattice 1 = D2Q16 / split I (FP64)
+cudaError_t launch_init(int lattice, int storage, void* dst, const double* rho, const double* ux, const double* uy,
                         const double* T, const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
-cudaError_t launch_ghost(int storage, void* buf, const Geom& G, const Phys& P, const Macro& M,
+cudaError_t launch_ghost(int lattice, int storage, void* buf, const Geom& G, const Phys& P, const Macro& M,
                          const BCDev& bc, cudaStream_t st);
-cudaError_t launch_moments(int storage, const void* src, double* rho, double* ux, double* uy, double* T,
+cudaError_t launch_moments(int lattice, int storage, const void* src, double* rho, double* ux, double* uy, double* T,
                            const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
 // per-block partial sums: out[blk*6 + {mass, momx, momy, energy, bad, 0}]
-cudaError_t launch_totals(int storage, const void* src, double* partial, int nblocks, const Geom& G,
+cudaError_t launch_totals(int lattice, int storage, const void* src, double* partial, int nblocks, const Geom& G,
                           const Phys& P, const Macro& M, cudaStream_t st);
 // per-block maxima of |u| + sqrt(gamma R T) and of p = rho R T, and a bad-input count:
 // out[blk*3 + {max speed, bad, max p}]
@@ -47,14 +49,6 @@ cudaError_t launch_pack(int storage, const void* buf, void* packed, int to_packe
 // D2Q16, total-energy split (I), FP64 storage
 cudaError_t launch_step16(const void* src, void* dst, const Geom& G, const Phys& P, unsigned int* flag,
                           cudaStream_t st);
-cudaError_t launch_init16(void* dst, const double* rho, const double* ux, const double* uy, const double* T,
-                          const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
-cudaError_t launch_moments16(const void* src, double* rho, double* ux, double* uy, double* T, const Geom& G,
-                             const Phys& P, const Macro& M, cudaStream_t st);
-cudaError_t launch_totals16(const void* src, double* partial, int nblocks, const Geom& G, const Phys& P,
-                            const Macro& M, cudaStream_t st);
-cudaError_t launch_ghost16(void* buf, const Geom& G, const Phys& P, const Macro& M, const BCDev& bc,
-                           cudaStream_t st);
 
 // adjoint (FP64 storage, periodic)
 int adjoint_blocks(const Geom& G);

@@ -66,8 +66,11 @@ def oracle_grad(F, Pr, gamma, mu, dt, n, rho_t, T_t):
 @pytest.mark.parametrize("Pr", [0.71, 2.0, 1.0])
 def test_adjoint_matches_oracle_autograd(D, Pr):
     """Every gradient entry of the CUDA adjoint equals the oracle's discrete
-    adjoint (reverse-mode AD of the oracle) to 1e-10 of its field maximum,
-    on a ragged 13 x 11 periodic grid over 6 steps with checkpoints every 2."""
+    adjoint (reverse-mode AD of the oracle) to 1e-12 of its field maximum
+    (measured: at most 4e-14), on a ragged 13 x 11 periodic grid over 6 steps
+    with checkpoints every 2.  The parameter gradients are sums over every
+    cell and step of terms of both signs, whose cancellation magnifies the
+    rounding of the terms: 1e-10 relative (measured: at most 3e-11)."""
     F = I.random_smooth(13, 11, seed=21, amp=0.08, Ma=0.4)
     rho_t, T_t = targets(13, 11)
     dt, n = 2e-4, 6
@@ -77,11 +80,11 @@ def test_adjoint_matches_oracle_autograd(D, Pr):
     for k in ("rho0", "ux0", "uy0", "T0"):
         a = g[k].cpu().numpy()
         scale = np.abs(o[k]).max()
-        assert np.abs(a - o[k]).max() < 1e-10 * scale, (k, np.abs(a - o[k]).max() / scale)
+        assert np.abs(a - o[k]).max() < 1e-12 * scale, (k, np.abs(a - o[k]).max() / scale)
     for k in ("mu", "Pr", "gamma"):
         if Pr == 1.0 and k == "Pr":
             continue  # one-sided at Pr = 1 (the branch switches there)
-        assert abs(g[k] - o[k]) < 1e-9 * max(abs(o[k]), 1e-30), (k, g[k], o[k])
+        assert abs(g[k] - o[k]) < 1e-10 * max(abs(o[k]), 1e-30), (k, g[k], o[k])
 
 
 def test_adjoint_matches_central_differences(D):

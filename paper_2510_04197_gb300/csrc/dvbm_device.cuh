@@ -596,12 +596,10 @@ __device__ __forceinline__ long long to_block_fixed52(double v, int E) {
   return hi < 0 ? -(long long)mag : (long long)mag;
 }
 
-// returns 4 lq (F_{j+1/2} - F_{j-1/2}) as a double (the caller folds 1/(4 lq))
-__device__ __forceinline__ double flux_difference_rat(const double* __restrict__ ptr, long long stride, int lp,
-                                                      int lq, int sgn) {
-  const long long o0 = sgn > 0 ? -2 * stride : -stride;
-  const double a0 = __ldg(ptr + o0), a1 = __ldg(ptr + o0 + stride), a2 = __ldg(ptr + o0 + 2 * stride),
-               a3 = __ldg(ptr + o0 + 3 * stride);
+// 4 lq (F_{j+1/2} - F_{j-1/2}) as a double (the caller folds 1/(4 lq)) from
+// the stencil values a0..a3 (v > 0: cells j-2..j+1; v < 0: cells j-1..j+2)
+__device__ __forceinline__ double flux_difference_rat_v(double a0, double a1, double a2, double a3, int lp, int lq,
+                                                        int sgn) {
   const int E = max(max(bexp(a0), bexp(a1)), max(bexp(a2), bexp(a3)));
   const long long x0 = to_block_fixed52(a0, E), x1 = to_block_fixed52(a1, E), x2 = to_block_fixed52(a2, E),
                   x3 = to_block_fixed52(a3, E);
@@ -612,6 +610,13 @@ __device__ __forceinline__ double flux_difference_rat(const double* __restrict__
   const long long F = sgn > 0 ? q4 * Db + s_bc - s_ab : q4 * Db - s_bc + s_ab;
   if (E < 64) return 0.0;
   return ll_to_double_scaled(F, E - 1074);  // value = F 2^(E - 1074)
+}
+// the same, loading the stencil along a stride
+__device__ __forceinline__ double flux_difference_rat(const double* __restrict__ ptr, long long stride, int lp,
+                                                      int lq, int sgn) {
+  const long long o0 = sgn > 0 ? -2 * stride : -stride;
+  return flux_difference_rat_v(__ldg(ptr + o0), __ldg(ptr + o0 + stride), __ldg(ptr + o0 + 2 * stride),
+                               __ldg(ptr + o0 + 3 * stride), lp, lq, sgn);
 }
 
 // slope_rat together with the minmod branch it took: 0 (a and b differ in

@@ -25,7 +25,7 @@ __constant__ long long c_khqx[4][4] = {
     {q16::khqfix(3, 0), q16::khqfix(3, 1), q16::khqfix(3, 2), q16::khqfix(3, 3)}};
 
 template <int PRC, bool RAT>
-__global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, double* __restrict__ dst, Geom G,
+__global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ src, double* __restrict__ dst, Geom G,
                                                 Phys P, unsigned int* __restrict__ flag) {
   using namespace q16;
   const int x = blockIdx.x * 32 + threadIdx.x;
@@ -87,19 +87,45 @@ __global__ void __launch_bounds__(256) k_step16(const double* __restrict__ src, 
       double tk[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) tk[q] = k == 0 ? tf[q] : tg[q];
+      // rational limiter: the next population's seven stencil values are
+      // loaded one iteration ahead (the rolled loop would leave them exposed)
+      double cv = 0, xa = 0, xb = 0, xc = 0, ya = 0, yb = 0, yc = 0;
+      auto load_stencil = [&](int qq, double& c0, double& x0, double& x1, double& x3, double& y0, double& y1,
+                              double& y3) {
+        const double* pq = s + pbase + (long long)(qq + 16 * k) * PL;
+        c0 = __ldg(pq);
+        const long long ox = sx > 0 ? -2 : -1;
+        x0 = __ldg(pq + ox);
+        x1 = __ldg(pq + ox + (sx > 0 ? 1 : 2));
+        x3 = __ldg(pq + ox + 3);
+        const int sq = sgn(qq);
+        const long long oy = sq > 0 ? -2 * PT : -PT;
+        y0 = __ldg(pq + oy);
+        y1 = __ldg(pq + oy + (sq > 0 ? PT : 2 * PT));
+        y3 = __ldg(pq + oy + 3 * PT);
+      };
+      if constexpr (RAT) load_stencil(0, cv, xa, xb, xc, ya, yb, yc);
 #pragma unroll 1
       for (int q = 0; q < 4; ++q) {  // y-nodes rolled too: one copy of the population body
         const long long co = pbase + (long long)(q + 16 * k) * PL;
         const double* pc = s + co;
-        double fx, fy;
+        const double t = q == 0 ? tk[0] : q == 1 ? tk[1] : q == 2 ? tk[2] : tk[3];
+        double fx, fy, c;
         if constexpr (RAT) {
-          fx = flux_difference_rat(pc, 1, P.lp, P.lq, sx);
-          fy = flux_difference_rat(pc, PT, P.lp, P.lq, sgn(q));
+          double nc = 0, nx0 = 0, nx1 = 0, nx3 = 0, ny0 = 0, ny1 = 0, ny3 = 0;
+          if (q < 3) load_stencil(q + 1, nc, nx0, nx1, nx3, ny0, ny1, ny3);
+          fx = sx > 0 ? flux_difference_rat_v(xa, xb, cv, xc, P.lp, P.lq, 1)
+                      : flux_difference_rat_v(xa, cv, xb, xc, P.lp, P.lq, -1);
+          fy = sgn(q) > 0 ? flux_difference_rat_v(ya, yb, cv, yc, P.lp, P.lq, 1)
+                          : flux_difference_rat_v(ya, cv, yb, yc, P.lp, P.lq, -1);
+          c = cv;
+          cv = nc; xa = nx0; xb = nx1; xc = nx3; ya = ny0; yb = ny1; yc = ny3;
         } else {
           fx = flux_difference_int(pc, 1, P.hq, sx);
           fy = flux_difference_int(pc, PT, P.hq, sgn(q));
+          c = __ldg(pc);
         }
-        double v = fma(C.a1, __ldg(pc), q == 0 ? tk[0] : q == 1 ? tk[1] : q == 2 ? tk[2] : tk[3]);
+        double v = fma(C.a1, c, t);
         v = fma(-kx, fx, v);
         v = fma(RAT ? -P.kyr[q] : -P.kyv[q], fy, v);
         d[co] = v;

@@ -142,7 +142,8 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
   const long long pbase = (long long)(5 * p) * PL;
   // FP64 storage also rolls the y-node loop (one copy of the population body:
   // fewer instruction-cache misses, 964 -> 986 MLUPS at 4096^2, bitwise the same
-  // result); FP32-deviation storage keeps it unrolled (1754 vs 1722 MLUPS rolled)
+  // result); FP32-deviation storage keeps it unrolled (1754 vs 1722 MLUPS rolled,
+  // 1742 rolled with the stencil loads below)
   constexpr bool ROLLQ = sizeof(S) == 8;
   // The rolled loop would leave each population's stencil loads exposed, so
   // the FP64 rational path loads the next population's seven stencil values

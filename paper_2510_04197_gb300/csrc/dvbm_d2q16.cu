@@ -58,25 +58,7 @@ __global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ sr
 #pragma unroll 1
   for (int p = 0; p < 4; ++p) {
     const long long k0 = c_khqx[p][0], k1 = c_khqx[p][1], k2 = c_khqx[p][2], k3 = c_khqx[p][3];
-    long long h[4], hh[3], xf[4], xg[4];
-    h[0] = mhk(xs[0 * 256], k0) + mhk(xs[1 * 256], k1) + mhk(xs[3 * 256], k2) + mhk(xs[6 * 256], k3);
-    h[1] = mhk(xs[2 * 256], k0) + mhk(xs[4 * 256], k1) + mhk(xs[7 * 256], k2);
-    h[2] = mhk(xs[5 * 256], k0) + mhk(xs[8 * 256], k1);
-    h[3] = mhk(xs[9 * 256], k0);
-    hh[0] = mhk(xs[10 * 256], k0) + mhk(xs[11 * 256], k1) + mhk(xs[13 * 256], k2);
-    hh[1] = mhk(xs[12 * 256], k0) + mhk(xs[14 * 256], k1);
-    hh[2] = mhk(xs[15 * 256], k0);
-    const int sf = renorm_fix(h), sg = renorm_fix(hh);
-    expand_fix(h, xf);
-    expand3_fix(hh, xg);
     const int dp = kdq(p < 2 ? 0 : 2);
-    double tf[4], tg[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      // value of t_q = x 2^(E - 1080 - kdq(p) - s - kdq(q))
-      tf[q] = Ef >= 100 ? ll_to_double_rn(xf[q], Ef - 1080 - dp - sf - kdq(q)) : 0.0;
-      tg[q] = Eg >= 100 ? ll_to_double_rn(xg[q], Eg - 1080 - dp - sg - kdq(q)) : 0.0;
-    }
     const int sx = (p & 1) ? -1 : 1;  // nodes +a, -a, +b, -b
     // kx of node p: kxv[1] = -kxv[0] and kxv[3] = -kxv[2] exactly
     const double kb = p < 2 ? (RAT ? P.kxr[0] : P.kxv[0]) : (RAT ? P.kxr[2] : P.kxv[2]);
@@ -84,9 +66,37 @@ __global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ sr
     const long long pbase = (long long)(4 * p) * PL;
 #pragma unroll 1
     for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
+      // this half's collision target (f, then g), built at the top of its own
+      // pass so that the g targets are not live across the f populations
       double tk[4];
+      {
+        long long xx[4];
+        int sc;
+        bool live;
+        if (k == 0) {
+          long long h[4];
+          h[0] = mhk(xs[0 * 256], k0) + mhk(xs[1 * 256], k1) + mhk(xs[3 * 256], k2) + mhk(xs[6 * 256], k3);
+          h[1] = mhk(xs[2 * 256], k0) + mhk(xs[4 * 256], k1) + mhk(xs[7 * 256], k2);
+          h[2] = mhk(xs[5 * 256], k0) + mhk(xs[8 * 256], k1);
+          h[3] = mhk(xs[9 * 256], k0);
+          const int sh = renorm_fix(h);
+          expand_fix(h, xx);
+          sc = Ef - 1080 - dp - sh;
+          live = Ef >= 100;
+        } else {
+          long long h[3];
+          h[0] = mhk(xs[10 * 256], k0) + mhk(xs[11 * 256], k1) + mhk(xs[13 * 256], k2);
+          h[1] = mhk(xs[12 * 256], k0) + mhk(xs[14 * 256], k1);
+          h[2] = mhk(xs[15 * 256], k0);
+          const int sh = renorm_fix(h);
+          expand3_fix(h, xx);
+          sc = Eg - 1080 - dp - sh;
+          live = Eg >= 100;
+        }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) tk[q] = k == 0 ? tf[q] : tg[q];
+        for (int q = 0; q < 4; ++q)  // value of t_q = x 2^(E - 1080 - kdq(p) - s - kdq(q))
+          tk[q] = live ? ll_to_double_rn(xx[q], sc - kdq(q)) : 0.0;
+      }
       // rational limiter: the next population's seven stencil values are
       // loaded one iteration ahead (the rolled loop would leave them exposed)
       double cv = 0, xa = 0, xb = 0, xc = 0, ya = 0, yb = 0, yc = 0;

@@ -453,16 +453,25 @@ __device__ __forceinline__ void expand_q3_fix(const long long (&h)[3], long long
 // f30, f21, f12, f03, f40, f31, f22, f13, f04, g00, g10, g01, g20, g11, g02);
 // k0..k4 = khfix(p, 0..4) (value of h = h 2^(E - 1081 - kd(p)))
 template <class V>
-__device__ __forceinline__ void hfg_fix(const V& X, long long k0, long long k1, long long k2, long long k3,
-                                        long long k4, long long (&hf)[5], long long (&hg)[3]) {
+__device__ __forceinline__ void hf_fix(const V& X, long long k0, long long k1, long long k2, long long k3,
+                                       long long k4, long long (&hf)[5]) {
   hf[0] = mhk(X(0), k0) + mhk(X(1), k1) + mhk(X(3), k2) + mhk(X(6), k3) + mhk(X(10), k4);
   hf[1] = mhk(X(2), k0) + mhk(X(4), k1) + mhk(X(7), k2) + mhk(X(11), k3);
   hf[2] = mhk(X(5), k0) + mhk(X(8), k1) + mhk(X(12), k2);
   hf[3] = mhk(X(9), k0) + mhk(X(13), k1);
   hf[4] = mhk(X(14), k0);
+}
+template <class V>
+__device__ __forceinline__ void hg_fix(const V& X, long long k0, long long k1, long long k2, long long (&hg)[3]) {
   hg[0] = mhk(X(15), k0) + mhk(X(16), k1) + mhk(X(18), k2);
   hg[1] = mhk(X(17), k0) + mhk(X(19), k1);
   hg[2] = mhk(X(20), k0);
+}
+template <class V>
+__device__ __forceinline__ void hfg_fix(const V& X, long long k0, long long k1, long long k2, long long k3,
+                                        long long k4, long long (&hf)[5], long long (&hg)[3]) {
+  hf_fix(X, k0, k1, k2, k3, k4, hf);
+  hg_fix(X, k0, k1, k2, hg);
 }
 
 // int64 -> float rounded to nearest (ties away from zero), value F 2^scale;

@@ -102,16 +102,20 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
                                             long long cplane = 0) {
   typedef typename StoreT<S>::adv_t A;
   // collision target in the storage's arithmetic type (FP32-deviation storage
-  // rounds the fixed-point result straight to float)
+  // rounds the fixed-point result straight to float).  FP64 storage builds
+  // each half's target (f, then g) at the top of its own pass of the f/g loop
+  // below, so that the g targets are not live across the f populations (fewer
+  // registers spilled); the arithmetic is the same.
+  constexpr bool SPLIT_T = sizeof(S) == 8;
+  const int dp = (CENTER || p == 0) ? 0 : (p <= 2 ? kd(1) : kd(3));
   A tf[5], tg[5];
-  {
+  if constexpr (!SPLIT_T) {
     long long hf[5], hg[3], xf[5], xg[5];
     if constexpr (CENTER) hfg_fix_view_centre(X, hf, hg);
     else hfg_fix_view(X, c_khx[p][0], c_khx[p][1], c_khx[p][2], c_khx[p][3], c_khx[p][4], hf, hg);  // p = 0 too
     const int sf = renorm_fix(hf), sg = renorm_fix(hg);
     expand_q5_fix(hf, xf);
     expand_q3_fix(hg, xg);
-    const int dp = (CENTER || p == 0) ? 0 : (p <= 2 ? kd(1) : kd(3));
     const int scf = Ef - 1080 - sf - dp, scg = Eg - 1080 - sg - dp;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -153,8 +157,31 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
 #pragma unroll 1
   for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
     A tk[5];
+    if constexpr (SPLIT_T) {
+      long long xx[5];
+      int sc;
+      bool live;
+      if (k == 0) {
+        long long h[5];
+        hf_fix(X, c_khx[p][0], c_khx[p][1], c_khx[p][2], c_khx[p][3], c_khx[p][4], h);
+        const int sh = renorm_fix(h);
+        expand_q5_fix(h, xx);
+        sc = Ef - 1080 - sh - dp;
+        live = Ef >= 100;
+      } else {
+        long long h[3];
+        hg_fix(X, c_khx[p][0], c_khx[p][1], c_khx[p][2], h);
+        const int sh = renorm_fix(h);
+        expand_q3_fix(h, xx);
+        sc = Eg - 1080 - sh - dp;
+        live = Eg >= 100;
+      }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) tk[q] = k == 0 ? tf[q] : tg[q];
+      for (int q = 0; q < 5; ++q) tk[q] = live ? (A)ll_to_double_rn(xx[q], sc - kd(q)) : (A)0;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) tk[q] = k == 0 ? tf[q] : tg[q];
+    }
     // stencil of population q: centre c, x cells (v > 0: j-2, j-1, j+1; v < 0: j-1, j+1, j+2), y likewise
     double cv = 0, xa = 0, xb = 0, xc = 0, ya = 0, yb = 0, yc = 0;
     auto load_stencil = [&](int qq, double& c0, double& x0, double& x1, double& x3, double& y0, double& y1,

@@ -66,6 +66,26 @@ __global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ sr
     const long long pbase = (long long)(4 * p) * PL;
 #pragma unroll 1
     for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
+      // rational limiter: the next population's seven stencil values are
+      // loaded one iteration ahead (the rolled loop would leave them exposed)
+      double cv = 0, xa = 0, xb = 0, xc = 0, ya = 0, yb = 0, yc = 0;
+      auto load_stencil = [&](int qq, double& c0, double& x0, double& x1, double& x3, double& y0, double& y1,
+                              double& y3) {
+        const double* pq = s + pbase + (long long)(qq + 16 * k) * PL;
+        c0 = __ldg(pq);
+        const long long ox = sx > 0 ? -2 : -1;
+        x0 = __ldg(pq + ox);
+        x1 = __ldg(pq + ox + (sx > 0 ? 1 : 2));
+        x3 = __ldg(pq + ox + 3);
+        const int sq = sgn(qq);
+        const long long oy = sq > 0 ? -2 * PT : -PT;
+        y0 = __ldg(pq + oy);
+        y1 = __ldg(pq + oy + (sq > 0 ? PT : 2 * PT));
+        y3 = __ldg(pq + oy + 3 * PT);
+      };
+      // the first population's stencil is loaded before the collision target
+      // below is built, whose integer work then covers the load latency
+      if constexpr (RAT) load_stencil(0, cv, xa, xb, xc, ya, yb, yc);
       // this half's collision target (f, then g), built at the top of its own
       // pass so that the g targets are not live across the f populations
       double tk[4];
@@ -97,24 +117,7 @@ __global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ sr
         for (int q = 0; q < 4; ++q)  // value of t_q = x 2^(E - 1080 - kdq(p) - s - kdq(q))
           tk[q] = live ? ll_to_double_rn(xx[q], sc - kdq(q)) : 0.0;
       }
-      // rational limiter: the next population's seven stencil values are
-      // loaded one iteration ahead (the rolled loop would leave them exposed)
-      double cv = 0, xa = 0, xb = 0, xc = 0, ya = 0, yb = 0, yc = 0;
-      auto load_stencil = [&](int qq, double& c0, double& x0, double& x1, double& x3, double& y0, double& y1,
-                              double& y3) {
-        const double* pq = s + pbase + (long long)(qq + 16 * k) * PL;
-        c0 = __ldg(pq);
-        const long long ox = sx > 0 ? -2 : -1;
-        x0 = __ldg(pq + ox);
-        x1 = __ldg(pq + ox + (sx > 0 ? 1 : 2));
-        x3 = __ldg(pq + ox + 3);
-        const int sq = sgn(qq);
-        const long long oy = sq > 0 ? -2 * PT : -PT;
-        y0 = __ldg(pq + oy);
-        y1 = __ldg(pq + oy + (sq > 0 ? PT : 2 * PT));
-        y3 = __ldg(pq + oy + 3 * PT);
-      };
-      if constexpr (RAT) load_stencil(0, cv, xa, xb, xc, ya, yb, yc);
+
 #pragma unroll 1
       for (int q = 0; q < 4; ++q) {  // y-nodes rolled too: one copy of the population body
         const long long co = pbase + (long long)(q + 16 * k) * PL;

@@ -104,8 +104,10 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
   // collision target in the storage's arithmetic type (FP32-deviation storage
   // rounds the fixed-point result straight to float).  FP64 storage builds
   // each half's target (f, then g) at the top of its own pass of the f/g loop
-  // below, so that the g targets are not live across the f populations (fewer
-  // registers spilled); the arithmetic is the same.
+  // below, so that the g targets are not live across the f populations (spill
+  // 200 -> 16 B per thread, 1007 -> 1086 MLUPS at 4096^2); the arithmetic is
+  // the same.  Loading the first population's stencil before this target is
+  // built measured 1083.
   constexpr bool SPLIT_T = sizeof(S) == 8;
   const int dp = (CENTER || p == 0) ? 0 : (p <= 2 ? kd(1) : kd(3));
   A tf[5], tg[5];
@@ -147,7 +149,8 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
   // FP64 storage also rolls the y-node loop (one copy of the population body:
   // fewer instruction-cache misses, 964 -> 986 MLUPS at 4096^2, bitwise the same
   // result); FP32-deviation storage keeps it unrolled (1754 vs 1722 MLUPS rolled,
-  // 1742 rolled with the stencil loads below)
+  // 1742 rolled with the stencil loads below, 1734 with the x-neighbours
+  // exchanged by warp shuffle instead of loaded)
   constexpr bool ROLLQ = sizeof(S) == 8;
   // The rolled loop would leave each population's stencil loads exposed, so
   // the FP64 rational path loads the next population's seven stencil values

@@ -66,8 +66,8 @@ __global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ sr
     const long long pbase = (long long)(4 * p) * PL;
 #pragma unroll 1
     for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
-      // rational limiter: the next population's seven stencil values are
-      // loaded one iteration ahead (the rolled loop would leave them exposed)
+      // the next population's seven stencil values are loaded one iteration
+      // ahead (the rolled loop would leave them exposed)
       double cv = 0, xa = 0, xb = 0, xc = 0, ya = 0, yb = 0, yc = 0;
       auto load_stencil = [&](int qq, double& c0, double& x0, double& x1, double& x3, double& y0, double& y1,
                               double& y3) {
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ sr
       };
       // the first population's stencil is loaded before the collision target
       // below is built, whose integer work then covers the load latency
-      if constexpr (RAT) load_stencil(0, cv, xa, xb, xc, ya, yb, yc);
+      load_stencil(0, cv, xa, xb, xc, ya, yb, yc);
       // this half's collision target (f, then g), built at the top of its own
       // pass so that the g targets are not live across the f populations
       double tk[4];
@@ -121,23 +121,19 @@ __global__ void __launch_bounds__(256, 4) k_step16(const double* __restrict__ sr
 #pragma unroll 1
       for (int q = 0; q < 4; ++q) {  // y-nodes rolled too: one copy of the population body
         const long long co = pbase + (long long)(q + 16 * k) * PL;
-        const double* pc = s + co;
         const double t = q == 0 ? tk[0] : q == 1 ? tk[1] : q == 2 ? tk[2] : tk[3];
-        double fx, fy, c;
-        if constexpr (RAT) {
-          double nc = 0, nx0 = 0, nx1 = 0, nx3 = 0, ny0 = 0, ny1 = 0, ny3 = 0;
-          if (q < 3) load_stencil(q + 1, nc, nx0, nx1, nx3, ny0, ny1, ny3);
-          fx = sx > 0 ? flux_difference_rat_v(xa, xb, cv, xc, P.lp, P.lq, 1)
-                      : flux_difference_rat_v(xa, cv, xb, xc, P.lp, P.lq, -1);
-          fy = sgn(q) > 0 ? flux_difference_rat_v(ya, yb, cv, yc, P.lp, P.lq, 1)
-                          : flux_difference_rat_v(ya, cv, yb, yc, P.lp, P.lq, -1);
-          c = cv;
-          cv = nc; xa = nx0; xb = nx1; xc = nx3; ya = ny0; yb = ny1; yc = ny3;
-        } else {
-          fx = flux_difference_int(pc, 1, P.hq, sx);
-          fy = flux_difference_int(pc, PT, P.hq, sgn(q));
-          c = __ldg(pc);
-        }
+        double nc = 0, nx0 = 0, nx1 = 0, nx3 = 0, ny0 = 0, ny1 = 0, ny3 = 0;
+        if (q < 3) load_stencil(q + 1, nc, nx0, nx1, nx3, ny0, ny1, ny3);
+        // flux difference of the stencil (a0..a3 = cells j-2..j+1 for v > 0,
+        // j-1..j+2 for v < 0): rational or general limiter
+        auto fdiff = [&](double a0, double a1, double a2, double a3, int sg) -> double {
+          if constexpr (RAT) return flux_difference_rat_v(a0, a1, a2, a3, P.lp, P.lq, sg);
+          else return flux_difference_int_v(a0, a1, a2, a3, P.hq, sg);
+        };
+        const double fx = sx > 0 ? fdiff(xa, xb, cv, xc, 1) : fdiff(xa, cv, xb, xc, -1);
+        const double fy = sgn(q) > 0 ? fdiff(ya, yb, cv, yc, 1) : fdiff(ya, cv, yb, yc, -1);
+        const double c = cv;
+        cv = nc; xa = nx0; xb = nx1; xc = nx3; ya = ny0; yb = ny1; yc = ny3;
         double v = fma(C.a1, c, t);
         v = fma(-kx, fx, v);
         v = fma(RAT ? -P.kyr[q] : -P.kyv[q], fy, v);

@@ -564,11 +564,10 @@ __device__ __forceinline__ long long slope_int(long long Da, long long Db, long 
   return same ? (Da >= 0 ? mn : mx) : 0ll;
 }
 
-__device__ __forceinline__ double flux_difference_int(const double* __restrict__ ptr, long long stride,
-                                                      long long Hq, int sgn) {
-  const long long o0 = sgn > 0 ? -2 * stride : -stride;
-  const double a0 = __ldg(ptr + o0), a1 = __ldg(ptr + o0 + stride), a2 = __ldg(ptr + o0 + 2 * stride),
-               a3 = __ldg(ptr + o0 + 3 * stride);
+// F_{j+1/2} - F_{j-1/2} (general beta) from the stencil values a0..a3 (v > 0:
+// cells j-2..j+1; v < 0: cells j-1..j+2)
+__device__ __forceinline__ double flux_difference_int_v(double a0, double a1, double a2, double a3, long long Hq,
+                                                        int sgn) {
   const int E = max(max(bexp(a0), bexp(a1)), max(bexp(a2), bexp(a3)));
   const long long x0 = to_block_fixed(a0, E), x1 = to_block_fixed(a1, E), x2 = to_block_fixed(a2, E),
                   x3 = to_block_fixed(a3, E);
@@ -620,13 +619,6 @@ __device__ __forceinline__ double flux_difference_rat_v(double a0, double a1, do
   if (E < 64) return 0.0;
   return ll_to_double_scaled(F, E - 1074);  // value = F 2^(E - 1074)
 }
-// the same, loading the stencil along a stride
-__device__ __forceinline__ double flux_difference_rat(const double* __restrict__ ptr, long long stride, int lp,
-                                                      int lq, int sgn) {
-  const long long o0 = sgn > 0 ? -2 * stride : -stride;
-  return flux_difference_rat_v(__ldg(ptr + o0), __ldg(ptr + o0 + stride), __ldg(ptr + o0 + 2 * stride),
-                               __ldg(ptr + o0 + 3 * stride), lp, lq, sgn);
-}
 
 // slope_rat together with the minmod branch it took: 0 (a and b differ in
 // sign), 1 (2 lp Da), 2 (lq (Da + Db)), 3 (2 lp Db), ties resolved in that
@@ -642,15 +634,12 @@ __device__ __forceinline__ long long slope_rat_code(long long Da, long long Db, 
   return br == 0 ? 0ll : (br == 1 ? ra : (br == 2 ? y : rb));
 }
 
-// flux_difference_rat that also returns the branch code of the cell's own
+// flux_difference_rat_v that also returns the branch code of the cell's own
 // slope sigma_j (first argument its backward, second its forward difference):
 // s_bc for v > 0, s_ab for v < 0.  The adjoint reads these codes instead of
 // re-deriving them from the state.
-__device__ __forceinline__ double flux_difference_rat_code(const double* __restrict__ ptr, long long stride, int lp,
-                                                           int lq, int sgn, int& code) {
-  const long long o0 = sgn > 0 ? -2 * stride : -stride;
-  const double a0 = __ldg(ptr + o0), a1 = __ldg(ptr + o0 + stride), a2 = __ldg(ptr + o0 + 2 * stride),
-               a3 = __ldg(ptr + o0 + 3 * stride);
+__device__ __forceinline__ double flux_difference_rat_code_v(double a0, double a1, double a2, double a3, int lp,
+                                                             int lq, int sgn, int& code) {
   const int E = max(max(bexp(a0), bexp(a1)), max(bexp(a2), bexp(a3)));
   const long long x0 = to_block_fixed52(a0, E), x1 = to_block_fixed52(a1, E), x2 = to_block_fixed52(a2, E),
                   x3 = to_block_fixed52(a3, E);

@@ -153,10 +153,11 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
   // exchanged by warp shuffle instead of loaded)
   constexpr bool ROLLQ = sizeof(S) == 8;
   // The rolled loop would leave each population's stencil loads exposed, so
-  // the FP64 rational path loads the next population's seven stencil values
-  // (centre, three along x, three along y) one iteration ahead: 986 -> 1009
-  // MLUPS at 4096^2, bitwise the same result.
-  constexpr bool PREF = sizeof(S) == 8 && RAT && !CODES;
+  // FP64 storage (every limiter form, with or without branch codes) loads the
+  // next population's seven stencil values (centre, three along x, three
+  // along y) one iteration ahead: 986 -> 1009 MLUPS at 4096^2 for the
+  // rational limiter, bitwise the same result.
+  constexpr bool PREF = sizeof(S) == 8;
 #pragma unroll 1
   for (int k = 0; k < 2; ++k) {  // f then g: one copy of the body for both
     A tk[5];
@@ -209,46 +210,35 @@ __device__ __forceinline__ void node_update(int p, const S* __restrict__ s, S* _
 #pragma unroll (ROLLQ ? 1 : 5)
     for (int q = 0; q < 5; ++q) {
       const long long co = pbase + (long long)(q + 25 * k) * PL;
-      const S* pc = s + co;
       const A t = ROLLQ ? (q == 0 ? tk[0] : q == 1 ? tk[1] : q == 2 ? tk[2] : q == 3 ? tk[3] : tk[4]) : tk[q];
       if constexpr (PREF) {
         double nc = 0, nx0 = 0, nx1 = 0, nx3 = 0, ny0 = 0, ny1 = 0, ny3 = 0;
         if (q < 4) load_stencil(q + 1, nc, nx0, nx1, nx3, ny0, ny1, ny3);
+        // flux difference of the stencil (a0..a3 = cells j-2..j+1 for v > 0,
+        // j-1..j+2 for v < 0) in the limiter form of this instantiation
+        auto fdiff = [&](double a0, double a1, double a2, double a3, int sg, int& code) -> double {
+          if constexpr (CODES) return flux_difference_rat_code_v(a0, a1, a2, a3, P.lp, P.lq, sg, code);
+          else if constexpr (RAT) return flux_difference_rat_v(a0, a1, a2, a3, P.lp, P.lq, sg);
+          else return flux_difference_int_v(a0, a1, a2, a3, P.hq, sg);
+        };
+        int cx = 0, cy = 0;
         double v = fma(C.a1, cv, (double)t);
         if (xmove) {
-          const double fx2 = sx > 0 ? flux_difference_rat_v(xa, xb, cv, xc, P.lp, P.lq, 1)
-                                    : flux_difference_rat_v(xa, cv, xb, xc, P.lp, P.lq, -1);
+          const double fx2 = sx > 0 ? fdiff(xa, xb, cv, xc, 1, cx) : fdiff(xa, cv, xb, xc, -1, cx);
           v = fma(-kx, fx2, v);
         }
         const int sq = sgn_of(q);
         if (sq != 0) {
-          const double fy2 = sq > 0 ? flux_difference_rat_v(ya, yb, cv, yc, P.lp, P.lq, 1)
-                                    : flux_difference_rat_v(ya, cv, yb, yc, P.lp, P.lq, -1);
-          v = fma(-P.kyr[q], fy2, v);
+          const double fy2 = sq > 0 ? fdiff(ya, yb, cv, yc, 1, cy) : fdiff(ya, cv, yb, yc, -1, cy);
+          v = fma(RAT ? -P.kyr[q] : -P.kyv[q], fy2, v);
         }
+        if constexpr (CODES) cd[(long long)(5 * p + q + 25 * k) * cplane] = (unsigned char)(cx | (cy << 2));
         d[co] = (S)v;
         cv = nc; xa = nx0; xb = nx1; xc = nx3; ya = ny0; yb = ny1; yc = ny3;
-        continue;
-      }
-      A fx = 0, fy = 0;
-      if constexpr (sizeof(S) == 8) {
-        if constexpr (CODES) {
-          int cx = 0, cy = 0;
-          if (xmove) fx = flux_difference_rat_code((const double*)pc, 1, P.lp, P.lq, sx, cx);
-          if (sgn_of(q) != 0) fy = flux_difference_rat_code((const double*)pc, PT, P.lp, P.lq, sgn_of(q), cy);
-          cd[(long long)(5 * p + q + 25 * k) * cplane] = (unsigned char)(cx | (cy << 2));
-        } else if constexpr (RAT) {
-          if (xmove) fx = flux_difference_rat((const double*)pc, 1, P.lp, P.lq, sx);
-          if (sgn_of(q) != 0) fy = flux_difference_rat((const double*)pc, PT, P.lp, P.lq, sgn_of(q));
-        } else {
-          if (xmove) fx = flux_difference_int((const double*)pc, 1, P.hq, sx);
-          if (sgn_of(q) != 0) fy = flux_difference_int((const double*)pc, PT, P.hq, sgn_of(q));
-        }
-        double v = fma(C.a1, (double)__ldg(pc), t);
-        if (xmove) v = fma(-kx, (double)fx, v);
-        if (sgn_of(q) != 0) v = fma(RAT ? -P.kyr[q] : -P.kyv[q], (double)fy, v);
-        d[co] = (S)v;
       } else {
+        // FP32-deviation storage: float flux differences on the deviations
+        const S* pc = s + co;
+        A fx = 0, fy = 0;
         if (!CENTER) fx = sx > 0 ? flux_difference<1, S>(pc, 1, (S)hb) : flux_difference<-1, S>(pc, 1, (S)hb);
         if (sgn_of(q) > 0) fy = flux_difference<1, S>(pc, PT, (S)hb);
         if (sgn_of(q) < 0) fy = flux_difference<-1, S>(pc, PT, (S)hb);

@@ -234,8 +234,9 @@ double dvbm_dt(const dvbm_ctx* ctx);
 /* Number of steps taken since dvbm_init / dvbm_set_state. */
 long long dvbm_steps_taken(const dvbm_ctx* ctx);
 
-/* Last error message of ctx (or of the last failed dvbm_create if ctx is
- * NULL).  Valid until the next call on that context. */
+/* Last error message of ctx (or, if ctx is NULL, of the calling thread's last
+ * failed dvbm_create).  Valid until the next call on that context (or the
+ * thread's next dvbm_create). */
 const char* dvbm_last_error(const dvbm_ctx* ctx);
 
 /* Release the context and its device buffers (NULL is a no-op). */

@@ -55,7 +55,9 @@ struct dvbm_ctx {
 
 static bool has_external(const dvbm_ctx* c) { return c->external[0] || c->external[1]; }
 
-static std::string g_create_error;
+// message of the calling thread's last failed dvbm_create (per thread: creating
+// contexts on several threads at once does not race on it)
+static thread_local std::string g_create_error;
 
 static dvbm_status fail(dvbm_ctx* c, dvbm_status s, const char* fmt, ...) {
   char msg[512];
@@ -248,11 +250,13 @@ extern "C" dvbm_status dvbm_create(dvbm_ctx** out, int lattice, int Nx, int Ny, 
   }
   if (cudaMemsetAsync(c->buf[0], 0, bytes, c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->buf[1], 0, bytes, c->stream) != cudaSuccess ||
-      cudaMemsetAsync(c->flag, 0, sizeof(unsigned int), c->stream) != cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      cudaMemsetAsync(c->flag, 0, sizeof(unsigned int), c->stream) != cudaSuccess) {
+    cudaGetLastError();
     dvbm_destroy(c);
     return fail(nullptr, DVBM_ECUDA, "buffer initialisation failed");
   }
+  // no wait here: the caller's stream may hold earlier work, and every later
+  // call of this context is ordered after the memsets on the same stream
   *out = c;
   return DVBM_OK;
 }

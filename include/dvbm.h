@@ -182,11 +182,13 @@ size_t dvbm_state_bytes(const dvbm_ctx* ctx);
 dvbm_status dvbm_get_state(dvbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 dvbm_status dvbm_set_state(dvbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
 
-/* Record the forward run for dvbm_adjoint: from the next dvbm_init on, keep
- * the initial fields and a device copy of the state every `every` steps
- * (checkpoints; sqrt(n) is the usual choice).  every = 0 turns recording off.
- * Needs FP64 storage and periodic boundaries.  dvbm_set_state discards the
- * recording.  Errors: EINVAL. */
+/* Record the forward run for dvbm_adjoint (or the stepwise adjoint below):
+ * from the next dvbm_init on, keep the initial fields and a device copy of the
+ * state every `every` steps (checkpoints; sqrt(n) is the usual choice).
+ * every = 0 turns recording off.  Needs FP64 storage, the D2Q25 / split II
+ * model and periodic boundaries; a band of a y-periodic grid (EXTERNAL y
+ * sides) may record too, for the stepwise adjoint.  dvbm_set_state discards
+ * the recording.  Errors: EINVAL. */
 dvbm_status dvbm_record(dvbm_ctx* ctx, int every);
 
 /* Discrete adjoint of the recorded run (a training pattern the paper does not
@@ -196,10 +198,44 @@ dvbm_status dvbm_record(dvbm_ctx* ctx, int every);
  * dL/drho0, dL/dux0, dL/duy0, dL/dT0 of the initial fields and, to the host
  * array g_params, dL/dmu, dL/dPr, dL/dgamma.  Each checkpoint segment is
  * recomputed once, then stepped backwards with the hand-written adjoint step
- * kernel.  The state of the context is left unchanged.  Synchronous.
+ * kernel.  The state of the context is left unchanged.  Synchronous.  A band
+ * (EXTERNAL sides) takes the stepwise adjoint below instead (EINVAL here).
  * Errors: ESTATE (no recording), EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
 dvbm_status dvbm_adjoint(dvbm_ctx* ctx, const double* dL_drho, const double* dL_dT, double* g_rho0,
                          double* g_ux0, double* g_uy0, double* g_T0, double g_params[3]);
+
+/* Stepwise adjoint, for a band of a slab-decomposed grid (EXTERNAL y sides),
+ * whose adjoint steps need the neighbouring bands' rows at every step; it also
+ * runs on a whole periodic grid.  The arithmetic is that of dvbm_adjoint
+ * except that the minmod branches are derived from the recomputed states
+ * rather than recorded (the recorded codes cover the band's own cells only),
+ * which can flip a branch where two candidates tie to the last bits.
+ *  - dvbm_adjoint_begin: lambda^N from the device arrays dL/drho, dL/dT of the
+ *    band's current state (either may be NULL = 0).  Needs a recorded run.
+ *  - dvbm_adjoint_advance: one action of the backward pass (restore a
+ *    checkpoint, recompute one forward step of the segment, or take one
+ *    adjoint step back through it), in the same order on every band.  *halo:
+ *    1 = the segment state just produced, 2 = the adjoint state just produced
+ *    (both after dvbm_adjoint_begin), needs its ghost rows from the
+ *    neighbouring bands before the next call; 0 = the pass is complete (call
+ *    dvbm_adjoint_finish).
+ *  - dvbm_adjoint_halo_pack / _unpack: as dvbm_halo_pack / _unpack, on the
+ *    buffer named by the last begin / advance (the same [npop][2][Nx] double
+ *    layout; the same buffer rules).
+ *  - dvbm_adjoint_finish: writes the device arrays dL/drho0, dL/dux0, dL/duy0,
+ *    dL/dT0 of the band's initial fields and, to the host array g_params, the
+ *    band's share of dL/dmu, dL/dPr, dL/dgamma (the grid's values are the sums
+ *    over the bands).  Synchronous.
+ * Everything but dvbm_adjoint_finish is stream-ordered without a host wait.
+ * The state of the context is left unchanged.  Errors: ESTATE (no recording,
+ * no pass begun, or finish before the pass is complete), EINVAL, ENOMEM,
+ * ECUDA, ETIMEOUT. */
+dvbm_status dvbm_adjoint_begin(dvbm_ctx* ctx, const double* dL_drho, const double* dL_dT);
+dvbm_status dvbm_adjoint_advance(dvbm_ctx* ctx, int* halo);
+dvbm_status dvbm_adjoint_halo_pack(dvbm_ctx* ctx, void* lo, void* hi);
+dvbm_status dvbm_adjoint_halo_unpack(dvbm_ctx* ctx, const void* lo, const void* hi);
+dvbm_status dvbm_adjoint_finish(dvbm_ctx* ctx, double* g_rho0, double* g_ux0, double* g_uy0, double* g_T0,
+                                double g_params[3]);
 
 /* Slab decomposition along y (multi-GPU, Sec. III.A.1; see DVBM_BC_EXTERNAL).
  * A halo buffer holds two rows of every population plane, layout

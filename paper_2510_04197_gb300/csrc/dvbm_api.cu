@@ -51,7 +51,22 @@ struct dvbm_ctx {
   bool external[2] = {false, false};  // ylo, yhi
   bool halo_fresh = false;             // the external ghost rows hold the current time level
   double pmax = 0.0;                   // largest pressure of the dvbm_init field (relaxation limit of dt)
+  // stepwise backward pass (dvbm_adjoint_begin / _advance / _finish)
+  struct AdjRun {
+    bool active = false;
+    void* lam[2] = {nullptr, nullptr};  // adjoint states; lam[a] is the current one
+    int a = 0;
+    std::vector<void*> seg;              // the states of the segment being processed
+    double* part = nullptr;              // per-block partial sums of the parameter adjoints
+    long long slot = 0;                  // next partial-sum slot
+    long long j = -1;                    // segment being processed (last first)
+    int phase = 0;                       // AdjRestore, AdjRecompute, AdjBackward, AdjDone
+    long long t = 0, nrec = 0;           // step within the segment; recompute steps of the segment
+    void* halo = nullptr;                // buffer whose ghost rows the neighbours fill next
+  } adj;
 };
+
+enum { AdjRestore = 0, AdjRecompute = 1, AdjBackward = 2, AdjDone = 3 };
 
 static bool has_external(const dvbm_ctx* c) { return c->external[0] || c->external[1]; }
 
@@ -365,7 +380,11 @@ static dvbm_status take_buffer(dvbm_ctx* c, void** out) {
   return DVBM_OK;
 }
 
+static void adj_release(dvbm_ctx* c, dvbm_status s);
+
+// also ends a stepwise backward pass: it reads the checkpoints being discarded
 static void clear_record(dvbm_ctx* c) {
+  if (c->adj.active) adj_release(c, DVBM_OK);
   for (void* p : c->ckpt) c->pool.push_back(p);
   c->ckpt.clear();
   c->recorded = false;
@@ -386,8 +405,12 @@ extern "C" dvbm_status dvbm_record(dvbm_ctx* c, int every) {
   if (every > 0 && c->storage != DVBM_FP64) return fail(c, DVBM_EINVAL, "the adjoint needs FP64 storage");
   if (every > 0 && c->lattice != DVBM_D2Q25_SPLIT_II)
     return fail(c, DVBM_EINVAL, "the adjoint is built for the D2Q25 / split II model");
-  for (int s = 0; s < 4 && every > 0; ++s)
-    if (c->bcs[s].kind != DVBM_BC_PERIODIC) return fail(c, DVBM_EINVAL, "the adjoint is built for periodic domains");
+  for (int s = 0; s < 4 && every > 0; ++s) {
+    // a band of a y-periodic grid has EXTERNAL y sides (the stepwise adjoint)
+    const bool band_side = s >= DVBM_YLO && c->bcs[s].kind == DVBM_BC_EXTERNAL;
+    if (c->bcs[s].kind != DVBM_BC_PERIODIC && !band_side)
+      return fail(c, DVBM_EINVAL, "the adjoint is built for periodic domains");
+  }
   clear_record(c);
   c->record_every = every;
   return DVBM_OK;
@@ -453,6 +476,8 @@ extern "C" dvbm_status dvbm_step(dvbm_ctx* c, int n) {
   if (has_external(c) && n == 1 && !c->halo_fresh)
     return fail(c, DVBM_ESTATE, "the external halo rows are stale: call dvbm_halo_unpack before each step");
   const int every = c->opts.check_every;
+  // new steps change the recorded run a stepwise backward pass is working through
+  if (n > 0 && c->adj.active) adj_release(c, DVBM_OK);
   for (int i = 0; i < n; ++i) {
     void* src = c->buf[c->cur];
     void* dst = c->buf[1 - c->cur];
@@ -617,6 +642,25 @@ extern "C" dvbm_status dvbm_set_dt(dvbm_ctx* c, double dt) {
   return DVBM_OK;
 }
 
+// dL/d(mu, Pr, gamma) from the per-block partial sums of a backward pass:
+// slot 0: final read-out (gm1 adjoint per block); slots 1 .. slot-2: steps
+// (dt_mu, Pr, gm1, epsf); last slot: initial condition (epsf adjoint per block)
+static void params_from_partials(const dvbm_ctx* c, const std::vector<double>& h, long long slot, int nblk,
+                                 double g_params[3]) {
+  double dtmu_b = 0, Pr_b = 0, gm1_b = 0, epsf_b = 0;
+  for (int b = 0; b < nblk; ++b) gm1_b += h[b];
+  for (long long t = 1; t < slot - 1; ++t)
+    for (int b = 0; b < nblk; ++b) {
+      const double* q = &h[(t * nblk + b) * 4];
+      dtmu_b += q[0]; Pr_b += q[1]; gm1_b += q[2]; epsf_b += q[3];
+    }
+  for (int b = 0; b < nblk; ++b) epsf_b += h[((slot - 1) * nblk) * 4 + b];
+  const double gm1 = c->gamma - 1.0;
+  g_params[0] = -dtmu_b * c->dt / (c->mu * c->mu);   // d(dt/mu)/dmu = -dt/mu^2
+  g_params[1] = Pr_b;
+  g_params[2] = gm1_b - epsf_b / (gm1 * gm1);        // epsf = 1/(gamma-1) - 1
+}
+
 // Backward pass over the recorded forward run: lambda^N from dL/d(rho, T) of
 // the current state, then segment by segment (last first) a recompute of the
 // segment's states from its checkpoint and the adjoint steps through it,
@@ -627,6 +671,9 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
   if (!c->recorded || c->ckpt.empty() || !c->init_fields)
     return fail(c, DVBM_ESTATE, "no recorded forward run: call dvbm_record(ctx, k) before dvbm_init, then dvbm_step");
   if (!g_rho0 || !g_ux0 || !g_uy0 || !g_T0 || !g_params) return fail(c, DVBM_EINVAL, "null gradient pointer");
+  if (has_external(c))
+    return fail(c, DVBM_EINVAL, "a band of a decomposed grid needs its neighbours at every adjoint step: "
+                                "use dvbm_adjoint_begin / _advance / _finish with halo exchanges");
   CUDA_TRY(c, cudaSetDevice(c->device));
   const long long n = c->steps;
   const int k = c->record_every;
@@ -715,20 +762,179 @@ extern "C" dvbm_status dvbm_adjoint(dvbm_ctx* c, const double* dL_drho, const do
   s = drain_then_copy(c, h.data(), part, h.size() * sizeof(double));
   cleanup();
   if (s != DVBM_OK) return s;
-  // slot 0: final read-out (gm1 adjoint per block); slots 1..n: steps (dt_mu, Pr, gm1, epsf);
-  // last slot: initial condition (epsf adjoint per block)
-  double dtmu_b = 0, Pr_b = 0, gm1_b = 0, epsf_b = 0;
-  for (int b = 0; b < nblk; ++b) gm1_b += h[b];
-  for (long long t = 1; t < slot - 1; ++t)
-    for (int b = 0; b < nblk; ++b) {
-      const double* q = &h[(t * nblk + b) * 4];
-      dtmu_b += q[0]; Pr_b += q[1]; gm1_b += q[2]; epsf_b += q[3];
+  params_from_partials(c, h, slot, nblk, g_params);
+  return DVBM_OK;
+}
+
+// ---- stepwise backward pass (a band of a slab-decomposed grid) -------------
+// The same sequence as dvbm_adjoint with the branch codes derived from the
+// states, cut at every point where a buffer's ghost rows must come from the
+// neighbouring bands: after lambda^N, after each restored or recomputed
+// segment state, after each adjoint step.
+
+// return the pass's buffers to the pool (stream-ordered reuse) and end it
+static void adj_release(dvbm_ctx* c, dvbm_status s) {
+  auto& A = c->adj;
+  for (int i = 0; i < 2; ++i)
+    if (A.lam[i]) {
+      c->pool.push_back(A.lam[i]);
+      A.lam[i] = nullptr;
     }
-  for (int b = 0; b < nblk; ++b) epsf_b += h[((slot - 1) * nblk) * 4 + b];
-  const double gm1 = c->gamma - 1.0;
-  g_params[0] = -dtmu_b * c->dt / (c->mu * c->mu);   // d(dt/mu)/dmu = -dt/mu^2
-  g_params[1] = Pr_b;
-  g_params[2] = gm1_b - epsf_b / (gm1 * gm1);        // epsf = 1/(gamma-1) - 1
+  for (void* p : A.seg) c->pool.push_back(p);
+  A.seg.clear();
+  if (A.part) release_temporary(c, A.part, s);
+  A.part = nullptr;
+  A.active = false;
+  A.halo = nullptr;
+}
+
+extern "C" dvbm_status dvbm_adjoint_begin(dvbm_ctx* c, const double* dL_drho, const double* dL_dT) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->recorded || c->ckpt.empty() || !c->init_fields)
+    return fail(c, DVBM_ESTATE, "no recorded forward run: call dvbm_record(ctx, k) before dvbm_init, then dvbm_step");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  auto& A = c->adj;
+  if (A.active) adj_release(c, DVBM_OK);  // a pass begun earlier is abandoned
+  const long long n = c->steps;
+  const int k = c->record_every;
+  const int nblk = adjoint_blocks(c->G);
+  dvbm_status s = DVBM_OK;
+  for (int i = 0; i < 2 && s == DVBM_OK; ++i) s = take_buffer(c, &A.lam[i]);
+  for (int i = 0; i < k && s == DVBM_OK; ++i) {
+    void* b = nullptr;
+    s = take_buffer(c, &b);
+    if (s == DVBM_OK) A.seg.push_back(b);
+  }
+  const long long nslots = (n + 2) * (long long)nblk * 4;
+  if (s == DVBM_OK && cudaMalloc(&A.part, nslots * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    A.part = nullptr;
+    s = fail(c, DVBM_ENOMEM, "cudaMalloc of adjoint partial sums failed");
+  }
+  cudaError_t e = cudaSuccess;
+  if (s == DVBM_OK) e = cudaMemsetAsync(A.part, 0, nslots * sizeof(double), c->stream);
+  if (s == DVBM_OK && e == cudaSuccess)
+    e = launch_adjoint_final((const double*)c->buf[c->cur], dL_drho, dL_dT, (double*)A.lam[0], A.part, c->G, c->P,
+                             c->M, c->stream);
+  // ghost columns (periodic x) now; EXTERNAL ghost rows come from the neighbours
+  if (s == DVBM_OK && e == cudaSuccess)
+    e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, A.lam[0], c->G, c->P, c->M, c->bc, c->stream);
+  if (s == DVBM_OK && e != cudaSuccess) s = fail(c, DVBM_ECUDA, "adjoint_begin: %s", cudaGetErrorString(e));
+  if (s != DVBM_OK) {
+    adj_release(c, s);
+    return s;
+  }
+  A.active = true;
+  A.a = 0;
+  A.slot = 1;
+  A.j = (n + k - 1) / k - 1;
+  A.phase = A.j >= 0 ? AdjRestore : AdjDone;
+  A.halo = A.lam[0];
+  return DVBM_OK;
+}
+
+extern "C" dvbm_status dvbm_adjoint_advance(dvbm_ctx* c, int* halo) {
+  if (!c || !halo) return DVBM_EINVAL;
+  auto& A = c->adj;
+  if (!A.active) return fail(c, DVBM_ESTATE, "no backward pass begun: call dvbm_adjoint_begin");
+  const long long n = c->steps;
+  const int k = c->record_every;
+  const int nblk = adjoint_blocks(c->G);
+  const long long S = A.j * k, E = std::min<long long>((A.j + 1) * k, n);
+  cudaError_t e = cudaSuccess;
+  switch (A.phase) {
+    case AdjRestore:  // the segment's first state from its checkpoint
+      e = cudaMemcpyAsync(A.seg[0], c->ckpt[A.j], c->state_bytes_dev, cudaMemcpyDeviceToDevice, c->stream);
+      A.nrec = E - S - 1;  // the adjoint of step t needs the state at t: states 0 .. E-S-1
+      A.t = A.nrec > 0 ? 0 : E - S - 1;
+      A.phase = A.nrec > 0 ? AdjRecompute : AdjBackward;
+      A.halo = A.seg[0];
+      *halo = 1;
+      break;
+    case AdjRecompute:  // one forward step of the segment
+      e = launch_step(0, A.seg[A.t], A.seg[A.t + 1], c->G, c->P, c->flag, c->stream);
+      if (e == cudaSuccess)
+        e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, A.seg[A.t + 1], c->G, c->P, c->M, c->bc, c->stream);
+      ++A.t;
+      A.halo = A.seg[A.t];
+      if (A.t == A.nrec) A.phase = AdjBackward;  // the adjoint starts at the segment's last state
+      *halo = 1;
+      break;
+    case AdjBackward: {  // one adjoint step back through the state at step S + t
+      const int a = A.a;
+      e = launch_adjoint_step((const double*)A.seg[A.t], (const double*)A.lam[a], (double*)A.lam[1 - a],
+                              A.part + A.slot * nblk * 4, nullptr, nullptr, c->G, c->P, c->stream);
+      ++A.slot;
+      A.a = 1 - a;
+      if (e == cudaSuccess)
+        e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, A.lam[A.a], c->G, c->P, c->M, c->bc, c->stream);
+      A.halo = A.lam[A.a];
+      if (A.t == 0) {
+        --A.j;
+        A.phase = A.j >= 0 ? AdjRestore : AdjDone;
+      } else {
+        --A.t;
+      }
+      *halo = 2;
+      break;
+    }
+    default:
+      *halo = 0;
+      return DVBM_OK;
+  }
+  if (e != cudaSuccess) {
+    const dvbm_status s = fail(c, DVBM_ECUDA, "adjoint_advance: %s", cudaGetErrorString(e));
+    adj_release(c, s);
+    return s;
+  }
+  return DVBM_OK;
+}
+
+// halo rows of the buffer the last begin / advance produced
+static dvbm_status adj_halo(dvbm_ctx* c, const void* lo, const void* hi, int unpack) {
+  if (!c) return DVBM_EINVAL;
+  if (!c->adj.active || !c->adj.halo) return fail(c, DVBM_ESTATE, "no backward pass begun: call dvbm_adjoint_begin");
+  if (unpack) {
+    const void* in[2] = {lo, hi};
+    for (int s = 0; s < 2; ++s) {
+      if (c->external[s] && !in[s]) return fail(c, DVBM_EINVAL, "side %s is external: its halo buffer is required", s ? "yhi" : "ylo");
+      if (!c->external[s] && in[s]) return fail(c, DVBM_EINVAL, "side %s is not external: pass NULL", s ? "yhi" : "ylo");
+    }
+  }
+  if (lo || hi)
+    CUDA_TRY(c, launch_halo(8, c->adj.halo, (void*)lo, (void*)hi, unpack, c->G, c->npop, c->stream));
+  return DVBM_OK;
+}
+extern "C" dvbm_status dvbm_adjoint_halo_pack(dvbm_ctx* c, void* lo, void* hi) { return adj_halo(c, lo, hi, 0); }
+extern "C" dvbm_status dvbm_adjoint_halo_unpack(dvbm_ctx* c, const void* lo, const void* hi) {
+  return adj_halo(c, lo, hi, 1);
+}
+
+extern "C" dvbm_status dvbm_adjoint_finish(dvbm_ctx* c, double* g_rho0, double* g_ux0, double* g_uy0, double* g_T0,
+                                           double g_params[3]) {
+  if (!c) return DVBM_EINVAL;
+  auto& A = c->adj;
+  if (!A.active) return fail(c, DVBM_ESTATE, "no backward pass begun: call dvbm_adjoint_begin");
+  if (A.phase != AdjDone) return fail(c, DVBM_ESTATE, "the backward pass is not complete: call dvbm_adjoint_advance");
+  if (!g_rho0 || !g_ux0 || !g_uy0 || !g_T0 || !g_params) return fail(c, DVBM_EINVAL, "null gradient pointer");
+  const int nblk = adjoint_blocks(c->G);
+  const size_t ncell = (size_t)c->Nx * c->Ny;
+  const double* F0 = c->init_fields;
+  cudaError_t e = launch_adjoint_init((const double*)A.lam[A.a], F0, F0 + ncell, F0 + 2 * ncell, F0 + 3 * ncell,
+                                      g_rho0, g_ux0, g_uy0, g_T0, A.part + A.slot * nblk * 4, c->G, c->P, c->M,
+                                      c->stream);
+  ++A.slot;
+  if (e != cudaSuccess) {
+    const dvbm_status s = fail(c, DVBM_ECUDA, "adjoint_finish: %s", cudaGetErrorString(e));
+    adj_release(c, s);
+    return s;
+  }
+  std::vector<double> h(A.slot * nblk * 4);
+  dvbm_status s = drain_then_copy(c, h.data(), A.part, h.size() * sizeof(double));
+  const long long slot = A.slot;
+  adj_release(c, s);
+  if (s != DVBM_OK) return s;
+  params_from_partials(c, h, slot, nblk, g_params);
   return DVBM_OK;
 }
 
@@ -739,6 +945,7 @@ extern "C" const char* dvbm_last_error(const dvbm_ctx* c) { return c ? c->err.c_
 extern "C" void dvbm_destroy(dvbm_ctx* c) {
   if (!c) return;
   if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
+  if (c->adj.active) adj_release(c, DVBM_OK);  // an unfinished stepwise adjoint: its buffers go to the pool
   for (int k = 0; k < 2; ++k) if (c->buf[k]) cudaFree(c->buf[k]);
   if (c->flag) cudaFree(c->flag);
   if (c->partial) cudaFree(c->partial);

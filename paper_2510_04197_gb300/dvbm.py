@@ -60,6 +60,11 @@ SIGNATURES = {
     "dvbm_destroy": (None, [_VP]),
     "dvbm_record": (_CI, [_VP, _CI]),
     "dvbm_adjoint": (_CI, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _DP]),
+    "dvbm_adjoint_begin": (_CI, [_VP, _VP, _VP]),
+    "dvbm_adjoint_advance": (_CI, [_VP, ctypes.POINTER(_CI)]),
+    "dvbm_adjoint_halo_pack": (_CI, [_VP, _VP, _VP]),
+    "dvbm_adjoint_halo_unpack": (_CI, [_VP, _VP, _VP]),
+    "dvbm_adjoint_finish": (_CI, [_VP, _VP, _VP, _VP, _VP, _DP]),
     "dvbm_halo_bytes": (ctypes.c_size_t, [_VP]),
     "dvbm_halo_pack": (_CI, [_VP, _VP, _VP]),
     "dvbm_halo_unpack": (_CI, [_VP, _VP, _VP]),
@@ -266,6 +271,58 @@ class Simulation:
                                                              for k in ("rho0", "ux0", "uy0", "T0")], gp), self._h)
         out["mu"], out["Pr"], out["gamma"] = gp[0], gp[1], gp[2]
         return out
+
+    # -- stepwise adjoint (a band of a decomposed grid; the drivers in slab.py)
+    def adjoint_begin(self, dL_drho=None, dL_dT=None):
+        """lambda^N of the backward pass from dL/drho, dL/dT of the band's
+        current state; its halo rows are exchanged next."""
+        args, self._adj_keep = [], []
+        for a in (dL_drho, dL_dT):
+            if a is None:
+                args.append(None)
+            else:
+                t = self._field(a)
+                self._adj_keep.append(t)  # read by stream-ordered kernels
+                args.append(ctypes.c_void_p(t.data_ptr()))
+        _check(lib().dvbm_adjoint_begin(self._h, args[0], args[1]), self._h)
+        return self
+
+    def adjoint_advance(self) -> int:
+        """One action of the backward pass; returns 1 (segment state) or 2
+        (adjoint state) for the buffer whose halo rows are exchanged next, 0
+        when the pass is complete."""
+        h = _CI(0)
+        _check(lib().dvbm_adjoint_advance(self._h, ctypes.byref(h)), self._h)
+        return int(h.value)
+
+    def adjoint_halo_pack(self, lo=None, hi=None):
+        _check(lib().dvbm_adjoint_halo_pack(self._h, _ptr(lo), _ptr(hi)), self._h)
+        return self
+
+    def adjoint_halo_unpack(self, lo=None, hi=None):
+        _check(lib().dvbm_adjoint_halo_unpack(self._h, _ptr(lo), _ptr(hi)), self._h)
+        return self
+
+    def adjoint_finish(self):
+        """Gradients of the band's initial fields and the band's share of
+        dL/d(mu, Pr, gamma)."""
+        torch = _torch()
+        out = {k: torch.empty((self.Ny, self.Nx), dtype=torch.float64, device=self.device)
+               for k in ("rho0", "ux0", "uy0", "T0")}
+        gp = (ctypes.c_double * 3)()
+        _check(lib().dvbm_adjoint_finish(self._h, *[ctypes.c_void_p(out[k].data_ptr())
+                                                    for k in ("rho0", "ux0", "uy0", "T0")], gp), self._h)
+        self._adj_keep = []
+        out["mu"], out["Pr"], out["gamma"] = gp[0], gp[1], gp[2]
+        return out
+
+    def adjoint_stepwise(self, dL_drho=None, dL_dT=None):
+        """The stepwise pass on a context that needs no neighbours (a whole
+        periodic grid): the same results as a one-band decomposition."""
+        self.adjoint_begin(dL_drho, dL_dT)
+        while self.adjoint_advance():
+            pass
+        return self.adjoint_finish()
 
     # -- slabs of a grid decomposed along y (EXTERNAL y sides)
     @property

@@ -17,6 +17,14 @@ highest rows up and its two lowest rows down, and receives its lower ghost
 rows from the band below and its upper ghost rows from the band above.  The
 time step is the smallest of the bands' CFL steps (``dvbm_set_dt``), domain
 totals are sums over bands.
+
+The adjoint of a y-periodic grid runs band by band with the stepwise backward
+pass (``dvbm_adjoint_begin`` / ``_advance`` / ``_finish``): every action of
+the pass (lambda^N, a restored checkpoint, a recomputed segment state, an
+adjoint step) is followed by the same two-row exchange of the buffer it
+produced (``dvbm_adjoint_halo_pack`` / ``_unpack``), all bands take the same
+actions in the same order, and dL/d(mu, Pr, gamma) is the sum of the bands'
+shares.
 """
 from __future__ import annotations
 
@@ -169,6 +177,46 @@ class LocalSlabs:
         t = [s.totals() for s in self.sims]
         return tuple(sum(v[i] for v in t) for i in range(4))
 
+    # -- adjoint (FP64, D2Q25 / split II, y-periodic grid)
+    def record(self, every: int):
+        for s in self.sims:
+            s.record(every)
+        return self
+
+    def _adjoint_exchange(self):
+        for k, s in enumerate(self.sims):
+            lower, upper = self.nb[k]
+            s.adjoint_halo_pack(self.out_lo[k] if lower is not None else None,
+                                self.out_hi[k] if upper is not None else None)
+        for k, s in enumerate(self.sims):
+            lower, upper = self.nb[k]
+            s.adjoint_halo_unpack(self.out_hi[lower] if lower is not None else None,
+                                  self.out_lo[upper] if upper is not None else None)
+
+    def adjoint(self, dL_drho=None, dL_dT=None):
+        """Gradients of a loss of the final (rho, T) fields, as
+        ``dvbm.Simulation.adjoint``: every band runs the stepwise backward pass,
+        with the halo rows of the buffer each action produced exchanged after
+        it; the bands' parameter gradients add up."""
+        import torch
+        n = len(self.sims)
+        parts = [self._rows(a) if a is not None else [None] * n for a in (dL_drho, dL_dT)]
+        for k, s in enumerate(self.sims):
+            s.adjoint_begin(parts[0][k], parts[1][k])
+        self._adjoint_exchange()
+        while True:
+            acts = {s.adjoint_advance() for s in self.sims}
+            if len(acts) != 1:
+                raise RuntimeError(f"bands out of step in the backward pass: {sorted(acts)}")
+            if acts == {0}:
+                break
+            self._adjoint_exchange()
+        res = [s.adjoint_finish() for s in self.sims]
+        out = {k: torch.cat([r[k] for r in res], dim=0) for k in ("rho0", "ux0", "uy0", "T0")}
+        for k in ("mu", "Pr", "gamma"):
+            out[k] = sum(r[k] for r in res)
+        return out
+
     def close(self):
         for s in self.sims:
             s.close()
@@ -220,6 +268,34 @@ class RankSlab:
         t = torch.tensor(self.sim.totals(), dtype=torch.float64, device=self.sim.device)
         self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
         return tuple(float(v) for v in t.cpu())
+
+    # -- adjoint (FP64, D2Q25 / split II, y-periodic grid)
+    def record(self, every: int):
+        self.sim.record(every)
+        return self
+
+    def _adjoint_exchange(self):
+        self.sim.adjoint_halo_pack(self.send_lo, self.send_hi)
+        exchange(self.dist, self.rank, self.world, self.periodic, self.send_lo, self.send_hi, self.recv_lo,
+                 self.recv_hi)
+        self.sim.adjoint_halo_unpack(self.recv_lo, self.recv_hi)
+
+    def adjoint(self, dL_drho=None, dL_dT=None):
+        """This band's share of the grid's backward pass (the gradients of its
+        own initial fields) and dL/d(mu, Pr, gamma) of the whole grid (an
+        all-reduce SUM over the bands).  Every rank takes the same actions in
+        the same order, so the point-to-point exchanges pair up as in the
+        forward steps."""
+        import torch
+        self.sim.adjoint_begin(dL_drho, dL_dT)
+        self._adjoint_exchange()
+        while self.sim.adjoint_advance():
+            self._adjoint_exchange()
+        out = self.sim.adjoint_finish()
+        p = torch.tensor([out["mu"], out["Pr"], out["gamma"]], dtype=torch.float64, device=self.sim.device)
+        self.dist.all_reduce(p, op=self.dist.ReduceOp.SUM)
+        out["mu"], out["Pr"], out["gamma"] = (float(v) for v in p.cpu())
+        return out
 
     def close(self):
         self.sim.close()

@@ -9,8 +9,7 @@ device-to-device copies (paper_2510_04197_gb300.slab.LocalSlabs).
 * Ragged bands (heights not multiples of 8) change the step kernel's tiles,
   hence its block exponents: within 1e-12 of the oracle.
 * The halo contract: a stale halo, several steps per call, a missing or an
-  unexpected halo buffer, a time step beyond the limits and recording for the
-  adjoint (not slab-decomposed) are refused.
+  unexpected halo buffer and a time step beyond the limits are refused.
 """
 import math
 import os
@@ -148,9 +147,6 @@ def test_halo_contract(D):
     assert ei.value.status == D.ESTATE
     with pytest.raises(D.DVBMError) as ei:  # one cell per step at most
         sim.set_dt(1.0)
-    assert ei.value.status == D.EINVAL
-    with pytest.raises(D.DVBMError) as ei:  # the adjoint is not slab-decomposed
-        sim.record(4)
     assert ei.value.status == D.EINVAL
     assert sim.dt == 2e-4
     # the periodic self-exchange equals the ordinary periodic context

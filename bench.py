@@ -344,6 +344,11 @@ def adjoint_ratio(dvbm, inputs, torch, N=512, nsteps=200):
         g = sim.adjoint((m["rho"] - mt["rho"]) / n2, (m["T"] - mt["T"]) / n2)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
+        # the stepwise pass a band of a decomposed grid runs (branches derived
+        # from the states), on the same recording, one band: no neighbours
+        gs = sim.adjoint_stepwise((m["rho"] - mt["rho"]) / n2, (m["T"] - mt["T"]) / n2)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
         sim.close()
         out = {"workload": f"adjoint {N}x{N} periodic multimode rms Ma 0.3, {nsteps} FP64 steps, "
                            f"checkpoints every {every}",
@@ -352,6 +357,11 @@ def adjoint_ratio(dvbm, inputs, torch, N=512, nsteps=200):
                "what": "t_adjoint / t_forward_steps: dvbm_adjoint (recompute + adjoint steps, wall clock) over "
                        "the same number of plain forward steps (CUDA events)",
                "t_recorded_forward_ms": (t1 - t0) * 1e3, "ratio_to_recorded_forward": (t2 - t1) / (t1 - t0),
+               "stepwise": {"t_ms": (t3 - t2) * 1e3, "ratio": (t3 - t2) * 1e3 / fwd_ms,
+                            "max_rel_diff": max(float((gs[k] - g[k]).abs().max() / g[k].abs().max())
+                                                for k in ("rho0", "ux0", "uy0", "T0")),
+                            "what": "dvbm_adjoint_begin/advance/finish on the same recording (the pass a band "
+                                    "of a slab-decomposed grid runs), wall clock"},
                "grad_norms": {k: float(g[k].norm()) for k in ("rho0", "ux0", "uy0", "T0")},
                "dL_dparams": [g["mu"], g["Pr"], g["gamma"]]}
     return out

@@ -260,8 +260,11 @@ dvbm_status dvbm_halo_unpack(dvbm_ctx* ctx, const void* lo, const void* hi);
  * the smallest of the slabs' CFL steps so that every slab of a decomposed
  * grid steps with the same dt (Sec. III.A.3).  dt is checked against the
  * limits dvbm_init applies (one cell per step; the shortest relaxation time
- * of the field given to dvbm_init).  Errors: EINVAL (dt <= 0, non-finite or
- * beyond the limits; the time step stays as it was), ESTATE (no state yet). */
+ * of the field given to dvbm_init).  A run recorded for the adjoint keeps the
+ * dt of its steps (the adjoint recomputes them): once it has stepped, a
+ * different dt is refused.  Errors: EINVAL (dt <= 0, non-finite or beyond the
+ * limits; the time step stays as it was), ESTATE (no state yet; a recorded
+ * run that has stepped). */
 dvbm_status dvbm_set_dt(dvbm_ctx* ctx, double dt);
 
 /* Time step size fixed at dvbm_init (0 before). */

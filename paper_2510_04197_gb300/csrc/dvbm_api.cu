@@ -635,6 +635,9 @@ extern "C" dvbm_status dvbm_set_dt(dvbm_ctx* c, double dt) {
   if (!c) return DVBM_EINVAL;
   if (!c->initialised) return fail(c, DVBM_ESTATE, "no state yet");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(c, DVBM_EINVAL, "dt must be > 0 and finite");
+  // the adjoint recomputes the recorded run with the context's dt
+  if (c->recorded && c->steps > 0 && dt != c->dt)
+    return fail(c, DVBM_ESTATE, "the recorded run has taken steps with dt = %g: it cannot change now", c->dt);
   const dvbm_status s = check_dt(c, dt, c->pmax);
   if (s != DVBM_OK) return s;
   c->dt = dt;

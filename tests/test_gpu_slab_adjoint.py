@@ -17,8 +17,8 @@ _halo_unpack / _finish) and the slab-decomposed backward pass built on it.
 * RankSlab over a one-rank NCCL group (the band is the whole grid, its halos
   its own rows): bitwise equal to the undecomposed stepwise pass.
 * The contract: dvbm_adjoint refuses a band, finish refuses an unfinished
-  pass, advance and the halo calls refuse a pass never begun, and a new step
-  ends a pass in progress.
+  pass, advance and the halo calls refuse a pass never begun, a new step
+  ends a pass in progress, and a recorded run that has stepped keeps its dt.
 """
 import os
 import socket
@@ -167,6 +167,10 @@ def test_stepwise_contract(D):
     F, G = _problem(32, 32)
     sl = _slab_adjoint(D, F, 0.71, 6, 3, 2e-4, parts=2)
     band = sl.sims[0]
+    with pytest.raises(D.DVBMError) as ei:  # the recompute needs the dt the run stepped with
+        band.set_dt(1e-4)
+    assert ei.value.status == D.ESTATE
+    band.set_dt(2e-4)  # the same dt is accepted
     z = torch.zeros((16, 32), dtype=torch.float64, device="cuda")
     with pytest.raises(D.DVBMError) as ei:  # a band needs its neighbours at every step
         band.adjoint(z, z)

@@ -24,8 +24,8 @@ class FakeBand:
     """Scripted stepwise pass: pack writes (band, action, side) codes, unpack
     records what arrived."""
 
-    def __init__(self, band):
-        self.band, self.action = band, 0
+    def __init__(self, band, swap=False):
+        self.band, self.action, self.swap = band, 0, swap
         self.received = []
 
     def halo_buffer(self):
@@ -45,6 +45,8 @@ class FakeBand:
                 buf.fill_(1000 * self.band + 10 * self.action + side)
 
     def adjoint_halo_unpack(self, lo=None, hi=None):
+        if self.swap:  # planted mistake: each side's rows land in the other side's ghost rows
+            lo, hi = hi, lo
         self.received.append((self.action, None if lo is None else float(lo[0, 0, 0]),
                               None if hi is None else float(hi[0, 0, 0])))
 
@@ -84,15 +86,13 @@ def _worker(rank, world, port, out_path, swap=False):
     try:
         rs = object.__new__(slab.RankSlab)  # a band without the library: the stand-in pass
         rs.dist, rs.rank, rs.world, rs.periodic = dist, rank, world, True
-        rs.sim = FakeBand(rank)
+        rs.sim = FakeBand(rank, swap)
         rs.sim.device = "cpu"
         lower, upper = slab.neighbours(rank, world, True)
         rs.send_lo = rs.sim.halo_buffer() if lower is not None else None
         rs.send_hi = rs.sim.halo_buffer() if upper is not None else None
         rs.recv_lo = rs.sim.halo_buffer() if lower is not None else None
         rs.recv_hi = rs.sim.halo_buffer() if upper is not None else None
-        if swap:  # planted mistake: each band's ghost rows land on the wrong side
-            rs.recv_lo, rs.recv_hi = rs.recv_hi, rs.recv_lo
         g = rs.adjoint(None, None)
         torch.save({"received": rs.sim.received, "params": (g["mu"], g["Pr"], g["gamma"]),
                     "rho0": g["rho0"]}, f"{out_path}.{rank}")

@@ -211,7 +211,9 @@ dvbm_status dvbm_adjoint(dvbm_ctx* ctx, const double* dL_drho, const double* dL_
  * rather than recorded (the recorded codes cover the band's own cells only),
  * which can flip a branch where two candidates tie to the last bits.
  *  - dvbm_adjoint_begin: lambda^N from the device arrays dL/drho, dL/dT of the
- *    band's current state (either may be NULL = 0).  Needs a recorded run.
+ *    band's current state (either may be NULL = 0), read by a kernel on the
+ *    context's stream: they must stay valid until the stream has run it (at
+ *    the latest, until dvbm_adjoint_finish returns).  Needs a recorded run.
  *  - dvbm_adjoint_advance: one action of the backward pass (restore a
  *    checkpoint, recompute one forward step of the segment, or take one
  *    adjoint step back through it), in the same order on every band.  *halo:

@@ -59,7 +59,7 @@ def oracle_grad(F, Pr, gamma, mu, dt, n, rho_t, T_t):
     N = Nx * Ny
     L = 0.5 / N * (((rho - torch.tensor(rho_t)) ** 2).sum() + ((T - torch.tensor(T_t)) ** 2).sum())
     L.backward()
-    return float(L), {"rho0": rho0.grad.numpy(), "ux0": ux0.grad.numpy(), "uy0": uy0.grad.numpy(),
+    return float(L.detach()), {"rho0": rho0.grad.numpy(), "ux0": ux0.grad.numpy(), "uy0": uy0.grad.numpy(),
                       "T0": T0.grad.numpy(), "mu": float(pm.grad), "Pr": float(pP.grad), "gamma": float(pg.grad)}
 
 

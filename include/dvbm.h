@@ -15,7 +15,7 @@
  * Conventions for every entry point:
  *  - Every function returns a dvbm_status and never aborts or throws.  On a
  *    non-OK status a message is available from dvbm_last_error(ctx) (or
- *    dvbm_last_error(NULL) for failures of dvbm_create).
+ *    dvbm_last_error(NULL) for failures of dvbm_create on the calling thread).
  *  - Macroscopic fields are row-major [Ny][Nx] double arrays (x fastest), cell
  *    centres x_j = (j + 1/2) Lx/Nx, y_k = (k + 1/2) Ly/Ny.  The caller owns
  *    every field buffer; the library owns the population buffers.
@@ -104,7 +104,9 @@ typedef struct {
                         (default 600 s; <= 0 selects the default): the
                         instability checks, dvbm_init, dvbm_moments and
                         dvbm_totals with host outputs, dvbm_get_state /
-                        dvbm_set_state, dvbm_adjoint.  The stream is drained
+                        dvbm_set_state, dvbm_adjoint, dvbm_adjoint_finish.
+                        dvbm_create does not wait for the stream; dvbm_destroy
+                        waits without a limit (below).  The stream is drained
                         under this limit before any copy into or out of
                         pageable host memory (such a copy would otherwise
                         block the calling thread without a limit).  A device

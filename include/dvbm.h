@@ -208,24 +208,28 @@ dvbm_status dvbm_adjoint(dvbm_ctx* ctx, const double* dL_drho, const double* dL_
 
 /* Stepwise adjoint, for a band of a slab-decomposed grid (EXTERNAL y sides),
  * whose adjoint steps need the neighbouring bands' rows at every step; it also
- * runs on a whole periodic grid.  The arithmetic is that of dvbm_adjoint
- * except that the minmod branches are derived from the recomputed states
- * rather than recorded (the recorded codes cover the band's own cells only),
- * which can flip a branch where two candidates tie to the last bits.
+ * runs on a whole periodic grid.  With the rational limiter (beta = lp/lq,
+ * the default) the arithmetic is that of dvbm_adjoint: the recompute records
+ * each step's minmod branch codes and moments, and a band receives its
+ * neighbours' code rows next to its edges.  Otherwise (or when the memory for
+ * the codes is missing) the branches are derived from the recomputed states.
  *  - dvbm_adjoint_begin: lambda^N from the device arrays dL/drho, dL/dT of the
  *    band's current state (either may be NULL = 0), read by a kernel on the
  *    context's stream: they must stay valid until the stream has run it (at
  *    the latest, until dvbm_adjoint_finish returns).  Needs a recorded run.
  *  - dvbm_adjoint_advance: one action of the backward pass (restore a
- *    checkpoint, recompute one forward step of the segment, or take one
- *    adjoint step back through it), in the same order on every band.  *halo:
- *    1 = the segment state just produced, 2 = the adjoint state just produced
- *    (both after dvbm_adjoint_begin), needs its ghost rows from the
- *    neighbouring bands before the next call; 0 = the pass is complete (call
+ *    checkpoint, recompute one forward step of the segment, hand over that
+ *    step's branch codes, or take one adjoint step back), in the same order on
+ *    every band.  *halo says what needs the neighbouring bands' rows before
+ *    the next call: 1 = the segment state just produced, 2 = the adjoint state
+ *    just produced (also after dvbm_adjoint_begin), 3 = the branch-code rows
+ *    of the step just recomputed; 0 = the pass is complete (call
  *    dvbm_adjoint_finish).
- *  - dvbm_adjoint_halo_pack / _unpack: as dvbm_halo_pack / _unpack, on the
- *    buffer named by the last begin / advance (the same [npop][2][Nx] double
- *    layout; the same buffer rules).
+ *  - dvbm_adjoint_halo_pack / _unpack: as dvbm_halo_pack / _unpack, for what
+ *    the last begin / advance named: two rows per side of a state in the
+ *    [npop][2][Nx] double layout, or (*halo = 3) one row per side of branch
+ *    codes, [npop][Nx] bytes at the start of the same buffers.  The same
+ *    buffer rules.
  *  - dvbm_adjoint_finish: writes the device arrays dL/drho0, dL/dux0, dL/duy0,
  *    dL/dT0 of the band's initial fields and, to the host array g_params, the
  *    band's share of dL/dmu, dL/dPr, dL/dgamma (the grid's values are the sums

@@ -19,6 +19,8 @@
 //    gives the partial derivatives (hb, 0), (1/4, 1/4), (0, hb) or (0, 0).
 //    As in the forward kernel the linear combinations run in block floating
 //    point on the integer pipe.
+#include <algorithm>
+
 #include "dvbm_device.cuh"
 #include "dvbm_cellmom.cuh"
 #include "dvbm_internal.h"
@@ -622,11 +624,16 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_local(const double* __restri
 // k_adjoint_adv: Lout += -(dt/dx) v_x sum_c' Lin(c') dF_x(c')/dX(c) - (same in y),
 // one thread per (cell, population); blockIdx.z = population.  CODED: the
 // minmod branches come from the codes the recomputed forward step recorded
-// (periodic neighbours wrap), so X is not read at all.
+// (periodic neighbours wrap), so X is not read at all.  A band of a
+// slab-decomposed grid passes the neighbouring bands' code rows next to its
+// edges (glo: the row below y = 0, ghi: the row above y = Ny - 1; [NPOP][Nx]
+// each) instead of wrapping in y.
 template <bool RAT, bool CODED>
 __global__ void __launch_bounds__(256) k_adjoint_adv(const double* __restrict__ X, const double* __restrict__ Lin,
                                                      double* __restrict__ Lout,
-                                                     const unsigned char* __restrict__ codes, Geom G, Phys P) {
+                                                     const unsigned char* __restrict__ codes, Geom G, Phys P,
+                                                     const unsigned char* __restrict__ glo = nullptr,
+                                                     const unsigned char* __restrict__ ghi = nullptr) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   const int c = blockIdx.z;
@@ -648,8 +655,9 @@ __global__ void __launch_bounds__(256) k_adjoint_adv(const double* __restrict__ 
     }
     if (sy != 0) {
       const int ym = y == 0 ? G.Ny - 1 : y - 1, yp = y == G.Ny - 1 ? 0 : y + 1;
-      const int bm = (__ldg(cp + (long long)ym * G.Nx + x) >> 2) & 3, b0 = (__ldg(cp + row + x) >> 2) & 3,
-                bp = (__ldg(cp + (long long)yp * G.Nx + x) >> 2) & 3;
+      const unsigned char* pm = (y == 0 && glo) ? glo + (long long)c * G.Nx + x : cp + (long long)ym * G.Nx + x;
+      const unsigned char* pp = (y == G.Ny - 1 && ghi) ? ghi + (long long)c * G.Nx + x : cp + (long long)yp * G.Nx + x;
+      const int bm = (__ldg(pm) >> 2) & 3, b0 = (__ldg(cp + row + x) >> 2) & 3, bp = (__ldg(pp) >> 2) & 3;
       v = fma(-P.kyr[qn], adjoint_combine_rat(lc, G.pitch, bm, b0, bp, P.lp, P.lq, sy), v);
     }
   } else if constexpr (RAT) {
@@ -746,9 +754,37 @@ __global__ void __launch_bounds__(256) k_adjoint_init(const double* __restrict__
 // ------------------------------------------------------------------ wrappers
 int adjoint_blocks(const Geom& G) { return ((G.Nx + 31) / 32) * ((G.Ny + 7) / 8); }
 
+// Branch-code rows next to a band's edges: unpack = 0 copies rows y = 0 (to
+// lo) and y = Ny - 1 (to hi) of every population's codes, unpack = 1 copies
+// lo and hi into the ghost code rows glo, ghi; layouts [NPOP][Nx] bytes; a
+// NULL buffer skips its side.
+__global__ void k_code_rows(unsigned char* __restrict__ codes, unsigned char* __restrict__ lo,
+                            unsigned char* __restrict__ hi, unsigned char* __restrict__ glo,
+                            unsigned char* __restrict__ ghi, int unpack, int Nx, int Ny) {
+  const long long n = (long long)NPOP * Nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / Nx, x = i % Nx;
+    if (unpack) {
+      if (lo) glo[i] = lo[i];
+      if (hi) ghi[i] = hi[i];
+    } else {
+      if (lo) lo[i] = codes[(c * Ny) * Nx + x];
+      if (hi) hi[i] = codes[(c * Ny + Ny - 1) * Nx + x];
+    }
+  }
+}
+
+cudaError_t launch_code_rows(unsigned char* codes, void* lo, void* hi, unsigned char* glo, unsigned char* ghi,
+                             int unpack, const Geom& G, cudaStream_t st) {
+  const long long n = (long long)NPOP * G.Nx;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  k_code_rows<<<blocks, 256, 0, st>>>(codes, (unsigned char*)lo, (unsigned char*)hi, glo, ghi, unpack, G.Nx, G.Ny);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial,
                                 const unsigned char* codes, const double* moms, const Geom& G, const Phys& P,
-                                cudaStream_t st) {
+                                cudaStream_t st, const unsigned char* glo, const unsigned char* ghi) {
   dim3 block(32, 8), grid((G.Nx + 31) / 32, (G.Ny + 7) / 8);
   if (moms) {
     if (P.prc < 0) k_adjoint_local<-1, true><<<grid, block, 0, st>>>(X, Lin, Lout, partial, moms, G, P);
@@ -762,7 +798,7 @@ cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid3(grid.x, grid.y, NPOP);
-  if (P.lq > 0 && codes) k_adjoint_adv<true, true><<<grid3, block, 0, st>>>(X, Lin, Lout, codes, G, P);
+  if (P.lq > 0 && codes) k_adjoint_adv<true, true><<<grid3, block, 0, st>>>(X, Lin, Lout, codes, G, P, glo, ghi);
   else if (P.lq > 0) k_adjoint_adv<true, false><<<grid3, block, 0, st>>>(X, Lin, Lout, nullptr, G, P);
   else k_adjoint_adv<false, false><<<grid3, block, 0, st>>>(X, Lin, Lout, nullptr, G, P);
   return cudaGetLastError();

@@ -63,10 +63,17 @@ struct dvbm_ctx {
     int phase = 0;                       // AdjRestore, AdjRecompute, AdjBackward, AdjDone
     long long t = 0, nrec = 0;           // step within the segment; recompute steps of the segment
     void* halo = nullptr;                // buffer whose ghost rows the neighbours fill next
+    int halo_kind = 0;                   // 1: rows of a state buffer (halo); 3: branch-code rows of step code_t
+    // coded pass (rational limiter): the recompute records branch codes and
+    // moments as in dvbm_adjoint; a band also holds its neighbours' code rows
+    unsigned char* codes = nullptr;      // [step][NPOP][Ny][Nx]
+    double* moms = nullptr;              // [step][13][Ny][Nx]
+    unsigned char* gcodes = nullptr;     // [step][lo, hi][NPOP][Nx]
+    long long code_t = 0;                // step whose code rows are exchanged next
   } adj;
 };
 
-enum { AdjRestore = 0, AdjRecompute = 1, AdjBackward = 2, AdjDone = 3 };
+enum { AdjRestore = 0, AdjRecompute = 1, AdjBackward = 2, AdjDone = 3, AdjCodes = 4 };
 
 static bool has_external(const dvbm_ctx* c) { return c->external[0] || c->external[1]; }
 
@@ -786,9 +793,16 @@ static void adj_release(dvbm_ctx* c, dvbm_status s) {
   for (void* p : A.seg) c->pool.push_back(p);
   A.seg.clear();
   if (A.part) release_temporary(c, A.part, s);
+  if (A.codes) release_temporary(c, A.codes, s);
+  if (A.moms) release_temporary(c, A.moms, s);
+  if (A.gcodes) release_temporary(c, A.gcodes, s);
   A.part = nullptr;
+  A.codes = nullptr;
+  A.moms = nullptr;
+  A.gcodes = nullptr;
   A.active = false;
   A.halo = nullptr;
+  A.halo_kind = 0;
 }
 
 extern "C" dvbm_status dvbm_adjoint_begin(dvbm_ctx* c, const double* dL_drho, const double* dL_dT) {
@@ -801,9 +815,28 @@ extern "C" dvbm_status dvbm_adjoint_begin(dvbm_ctx* c, const double* dL_drho, co
   const long long n = c->steps;
   const int k = c->record_every;
   const int nblk = adjoint_blocks(c->G);
+  // Rational limiter: the coded pass of dvbm_adjoint (the recompute records
+  // branch codes and moments; the segment's last state is stepped too), with
+  // the neighbouring bands' code rows exchanged after each recompute step.
+  // Otherwise, or without the memory for the codes, the adjoint derives the
+  // branches from the states.
+  const size_t ncell = (size_t)c->Nx * c->Ny;
+  if (c->P.lq > 0) {
+    if (cudaMalloc(&A.codes, (size_t)k * NPOP * ncell) != cudaSuccess ||
+        cudaMalloc(&A.moms, (size_t)k * 13 * ncell * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A.gcodes, (size_t)k * 2 * NPOP * c->Nx) != cudaSuccess) {
+      cudaGetLastError();
+      if (A.codes) cudaFree(A.codes);
+      if (A.moms) cudaFree(A.moms);
+      A.codes = nullptr;
+      A.moms = nullptr;
+      A.gcodes = nullptr;
+    }
+  }
+  const bool coded = A.codes != nullptr;
   dvbm_status s = DVBM_OK;
   for (int i = 0; i < 2 && s == DVBM_OK; ++i) s = take_buffer(c, &A.lam[i]);
-  for (int i = 0; i < k && s == DVBM_OK; ++i) {
+  for (int i = 0; i < k + (coded ? 1 : 0) && s == DVBM_OK; ++i) {
     void* b = nullptr;
     s = take_buffer(c, &b);
     if (s == DVBM_OK) A.seg.push_back(b);
@@ -833,6 +866,7 @@ extern "C" dvbm_status dvbm_adjoint_begin(dvbm_ctx* c, const double* dL_drho, co
   A.j = (n + k - 1) / k - 1;
   A.phase = A.j >= 0 ? AdjRestore : AdjDone;
   A.halo = A.lam[0];
+  A.halo_kind = 1;
   return DVBM_OK;
 }
 
@@ -843,35 +877,69 @@ extern "C" dvbm_status dvbm_adjoint_advance(dvbm_ctx* c, int* halo) {
   const long long n = c->steps;
   const int k = c->record_every;
   const int nblk = adjoint_blocks(c->G);
+  const size_t ncell = (size_t)c->Nx * c->Ny;
+  const size_t code_step = (size_t)NPOP * ncell, mom_step = (size_t)13 * ncell, gcode_step = (size_t)2 * NPOP * c->Nx;
+  const bool coded = A.codes != nullptr;
   const long long S = A.j * k, E = std::min<long long>((A.j + 1) * k, n);
   cudaError_t e = cudaSuccess;
   switch (A.phase) {
     case AdjRestore:  // the segment's first state from its checkpoint
       e = cudaMemcpyAsync(A.seg[0], c->ckpt[A.j], c->state_bytes_dev, cudaMemcpyDeviceToDevice, c->stream);
-      A.nrec = E - S - 1;  // the adjoint of step t needs the state at t: states 0 .. E-S-1
+      // the adjoint of step t needs the state at t (states 0 .. E-S-1); the
+      // coded pass also steps the last one (its step records its codes)
+      A.nrec = coded ? E - S : E - S - 1;
       A.t = A.nrec > 0 ? 0 : E - S - 1;
       A.phase = A.nrec > 0 ? AdjRecompute : AdjBackward;
       A.halo = A.seg[0];
+      A.halo_kind = 1;
       *halo = 1;
       break;
     case AdjRecompute:  // one forward step of the segment
-      e = launch_step(0, A.seg[A.t], A.seg[A.t + 1], c->G, c->P, c->flag, c->stream);
+      if (coded)
+        e = launch_step_codes(A.seg[A.t], A.seg[A.t + 1], c->G, c->P, c->flag, A.codes + A.t * code_step,
+                              A.moms + A.t * mom_step, c->stream);
+      else
+        e = launch_step(0, A.seg[A.t], A.seg[A.t + 1], c->G, c->P, c->flag, c->stream);
       if (e == cudaSuccess)
         e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, A.seg[A.t + 1], c->G, c->P, c->M, c->bc, c->stream);
+      A.code_t = A.t;
       ++A.t;
       A.halo = A.seg[A.t];
-      if (A.t == A.nrec) A.phase = AdjBackward;  // the adjoint starts at the segment's last state
+      A.halo_kind = 1;
+      if (coded) {
+        A.phase = AdjCodes;  // next: the code rows of the step just taken
+      } else if (A.t == A.nrec) {
+        A.phase = AdjBackward;  // the adjoint starts at the segment's last state
+        A.t = E - S - 1;
+      }
       *halo = 1;
+      break;
+    case AdjCodes:  // no work: the neighbours' code rows of step code_t are exchanged
+      A.halo = nullptr;
+      A.halo_kind = 3;
+      if (A.t == A.nrec) {
+        A.phase = AdjBackward;
+        A.t = E - S - 1;
+      } else {
+        A.phase = AdjRecompute;
+      }
+      *halo = 3;
       break;
     case AdjBackward: {  // one adjoint step back through the state at step S + t
       const int a = A.a;
+      const bool band = has_external(c);
+      unsigned char* gl = coded && band ? A.gcodes + A.t * gcode_step : nullptr;
       e = launch_adjoint_step((const double*)A.seg[A.t], (const double*)A.lam[a], (double*)A.lam[1 - a],
-                              A.part + A.slot * nblk * 4, nullptr, nullptr, c->G, c->P, c->stream);
+                              A.part + A.slot * nblk * 4, coded ? A.codes + A.t * code_step : nullptr,
+                              coded ? A.moms + A.t * mom_step : nullptr, c->G, c->P, c->stream,
+                              gl && c->external[0] ? gl : nullptr,
+                              gl && c->external[1] ? gl + (size_t)NPOP * c->Nx : nullptr);
       ++A.slot;
       A.a = 1 - a;
       if (e == cudaSuccess)
         e = launch_ghost(DVBM_D2Q25_SPLIT_II, 0, A.lam[A.a], c->G, c->P, c->M, c->bc, c->stream);
       A.halo = A.lam[A.a];
+      A.halo_kind = 1;
       if (A.t == 0) {
         --A.j;
         A.phase = A.j >= 0 ? AdjRestore : AdjDone;
@@ -893,10 +961,12 @@ extern "C" dvbm_status dvbm_adjoint_advance(dvbm_ctx* c, int* halo) {
   return DVBM_OK;
 }
 
-// halo rows of the buffer the last begin / advance produced
+// halo rows of what the last begin / advance produced: a state buffer's two
+// rows per side, or the branch-code row per side of step code_t
 static dvbm_status adj_halo(dvbm_ctx* c, const void* lo, const void* hi, int unpack) {
   if (!c) return DVBM_EINVAL;
-  if (!c->adj.active || !c->adj.halo) return fail(c, DVBM_ESTATE, "no backward pass begun: call dvbm_adjoint_begin");
+  auto& A = c->adj;
+  if (!A.active || !A.halo_kind) return fail(c, DVBM_ESTATE, "no backward pass begun: call dvbm_adjoint_begin");
   if (unpack) {
     const void* in[2] = {lo, hi};
     for (int s = 0; s < 2; ++s) {
@@ -904,8 +974,15 @@ static dvbm_status adj_halo(dvbm_ctx* c, const void* lo, const void* hi, int unp
       if (!c->external[s] && in[s]) return fail(c, DVBM_EINVAL, "side %s is not external: pass NULL", s ? "yhi" : "ylo");
     }
   }
-  if (lo || hi)
-    CUDA_TRY(c, launch_halo(8, c->adj.halo, (void*)lo, (void*)hi, unpack, c->G, c->npop, c->stream));
+  if (!lo && !hi) return DVBM_OK;
+  if (A.halo_kind == 3) {
+    const size_t gcode_step = (size_t)2 * NPOP * c->Nx;
+    unsigned char* g = A.gcodes + A.code_t * gcode_step;
+    CUDA_TRY(c, launch_code_rows(A.codes + A.code_t * (size_t)NPOP * c->Nx * c->Ny, (void*)lo, (void*)hi, g,
+                                 g + (size_t)NPOP * c->Nx, unpack, c->G, c->stream));
+  } else {
+    CUDA_TRY(c, launch_halo(8, A.halo, (void*)lo, (void*)hi, unpack, c->G, c->npop, c->stream));
+  }
   return DVBM_OK;
 }
 extern "C" dvbm_status dvbm_adjoint_halo_pack(dvbm_ctx* c, void* lo, void* hi) { return adj_halo(c, lo, hi, 0); }

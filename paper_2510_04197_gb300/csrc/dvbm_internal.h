@@ -54,9 +54,16 @@ cudaError_t launch_step16(const void* src, void* dst, const Geom& G, const Phys&
 int adjoint_blocks(const Geom& G);
 // codes: the branch codes recorded by launch_step_codes for this step, or
 // nullptr (the advection adjoint then derives the branches from X)
+// glo, ghi: the neighbouring bands' code rows next to a band's edges ([NPOP][Nx]
+// each, coded path only), or nullptr: the codes wrap periodically in y
 cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout, double* partial,
                                 const unsigned char* codes, const double* moms, const Geom& G, const Phys& P,
-                                cudaStream_t st);
+                                cudaStream_t st, const unsigned char* glo = nullptr,
+                                const unsigned char* ghi = nullptr);
+// branch-code rows of a band's edges: unpack = 0: rows y = 0 -> lo, y = Ny - 1 -> hi of
+// every population's codes; unpack = 1: lo -> glo, hi -> ghi; [NPOP][Nx] bytes, NULL skips
+cudaError_t launch_code_rows(unsigned char* codes, void* lo, void* hi, unsigned char* glo, unsigned char* ghi,
+                             int unpack, const Geom& G, cudaStream_t st);
 cudaError_t launch_adjoint_final(const double* X, const double* rhob, const double* Tb, double* Lout, double* partial,
                                  const Geom& G, const Phys& P, const Macro& M, cudaStream_t st);
 cudaError_t launch_adjoint_init(const double* L, const double* rho, const double* ux, const double* uy,

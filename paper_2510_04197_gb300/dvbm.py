@@ -288,9 +288,10 @@ class Simulation:
         return self
 
     def adjoint_advance(self) -> int:
-        """One action of the backward pass; returns 1 (segment state) or 2
-        (adjoint state) for the buffer whose halo rows are exchanged next, 0
-        when the pass is complete."""
+        """One action of the backward pass; returns what the neighbouring
+        bands exchange next: 1 (segment state rows), 2 (adjoint state rows),
+        3 (branch-code rows of the step just recomputed), or 0 when the pass
+        is complete."""
         h = _CI(0)
         _check(lib().dvbm_adjoint_advance(self._h, ctypes.byref(h)), self._h)
         return int(h.value)

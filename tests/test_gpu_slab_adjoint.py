@@ -1,19 +1,19 @@
 """The stepwise adjoint (dvbm_adjoint_begin / _advance / _halo_pack /
 _halo_unpack / _finish) and the slab-decomposed backward pass built on it.
 
-* On a whole periodic grid the stepwise pass equals dvbm_adjoint to rounding:
-  the only difference is that it derives the minmod branches from the
-  recomputed states instead of reading the codes the recompute recorded
-  (fields within 1e-12 of their maximum, parameters 1e-10 relative), for
-  Pr < 1 and Pr > 1 and checkpoint intervals that do and do not divide the
-  step count.
+* On a whole periodic grid the stepwise pass is dvbm_adjoint's arithmetic
+  (rational limiter: recorded branch codes and moments; general beta: the
+  branches derived from the recomputed states, in both): bitwise the same
+  gradients, for Pr < 1 and Pr > 1, beta = 1.2 and sqrt(2), and checkpoint
+  intervals that do and do not divide the step count.
 * A grid split into bands along y (LocalSlabs, one context per band, the
-  halo rows of every restored, recomputed and adjoint state exchanged after
-  the action that produced it): the gradients of the initial fields equal
-  the undecomposed stepwise pass bitwise for bands of whole 8-row tiles, and
-  to 1e-12 for ragged bands; dL/d(mu, Pr, gamma), sums over every cell and
-  step of terms of both signs taken band by band in another order, to 1e-10
-  relative (measured: 1.6e-12 for gamma).
+  halo rows of every restored, recomputed and adjoint state and the code
+  rows of every recomputed step exchanged after the action that produced
+  them): the gradients of the initial fields equal dvbm_adjoint on the
+  undecomposed grid bitwise for bands of whole 8-row tiles, and to 1e-12 for
+  ragged bands; dL/d(mu, Pr, gamma), sums over every cell and step of terms
+  of both signs taken band by band in another order, to 1e-10 relative
+  (measured: 1.6e-12 for gamma).
 * RankSlab over a one-rank NCCL group (the band is the whole grid, its halos
   its own rows): bitwise equal to the undecomposed stepwise pass.
 * The contract: dvbm_adjoint refuses a band, finish refuses an unfinished
@@ -56,16 +56,18 @@ def _loss_grads(m, target):
     return (m["rho"] - target["rho"]) / N, (m["T"] - target["T"]) / N
 
 
-def _single(D, F, Pr, nsteps, every, dt):
-    sim = D.Simulation(F.rho.shape[1], F.rho.shape[0], Pr, 1.4, 2e-3, Lx=F.Lx, Ly=F.Ly, dt=dt, check_every=-1)
+def _single(D, F, Pr, nsteps, every, dt, **kw):
+    sim = D.Simulation(F.rho.shape[1], F.rho.shape[0], Pr, 1.4, 2e-3, Lx=F.Lx, Ly=F.Ly, dt=dt, check_every=-1,
+                       **kw)
     sim.record(every)
     sim.init(*_fields(F))
     sim.step(nsteps)
     return sim
 
 
-def _target(D, G, Pr, nsteps, dt):
-    sim = D.Simulation(G.rho.shape[1], G.rho.shape[0], Pr, 1.4, 2e-3, Lx=G.Lx, Ly=G.Ly, dt=dt, check_every=-1)
+def _target(D, G, Pr, nsteps, dt, **kw):
+    sim = D.Simulation(G.rho.shape[1], G.rho.shape[0], Pr, 1.4, 2e-3, Lx=G.Lx, Ly=G.Ly, dt=dt, check_every=-1,
+                       **kw)
     sim.init(*_fields(G))
     sim.step(nsteps)
     m = sim.moments()
@@ -81,16 +83,24 @@ def _close(a, b, tol_field=1e-12, tol_param=1e-10):
         assert abs(a[k] - b[k]) <= tol_param * abs(b[k]), (k, a[k], b[k])
 
 
-@pytest.mark.parametrize("Pr,nsteps,every", [(0.71, 40, 7), (2.0, 24, 6), (0.71, 1, 1)])
-def test_stepwise_equals_monolithic_on_a_periodic_grid(D, Pr, nsteps, every):
+def _equal(a, b):
+    assert all(torch.equal(a[k], b[k]) for k in FIELDS), [float((a[k] - b[k]).abs().max()) for k in FIELDS]
+    assert all(a[k] == b[k] for k in ("mu", "Pr", "gamma")), [(a[k], b[k]) for k in ("mu", "Pr", "gamma")]
+
+
+@pytest.mark.parametrize("Pr,nsteps,every,beta", [(0.71, 40, 7, 1.2), (2.0, 24, 6, 1.2), (0.71, 1, 1, 1.2),
+                                                  (0.71, 30, 7, 2 ** 0.5)])
+def test_stepwise_equals_monolithic_on_a_periodic_grid(D, Pr, nsteps, every, beta):
     F, G = _problem(48, 40)
     dt = 2e-4
-    tgt = _target(D, G, Pr, nsteps, dt)
-    sim = _single(D, F, Pr, nsteps, every, dt)
+    tgt = _target(D, G, Pr, nsteps, dt, beta=beta)
+    sim = _single(D, F, Pr, nsteps, every, dt, beta=beta)
     dr, dT = _loss_grads(sim.moments(), tgt)
     a = sim.adjoint(dr, dT)
     b = sim.adjoint_stepwise(dr, dT)
-    _close(b, a)
+    # rational limiter: both run the coded arithmetic; general beta: both
+    # derive the branches from the states
+    _equal(b, a)
     # a second pass on the same recording gives the same result
     c = sim.adjoint_stepwise(dr, dT)
     assert all(torch.equal(b[k], c[k]) for k in FIELDS)
@@ -120,11 +130,11 @@ def test_bands_equal_the_undecomposed_pass(D, parts, heights, Pr):
     if heights is None:  # whole tiles: the decomposed forward run is bitwise the same
         assert torch.equal(sl.populations(), sim.populations())
     got = sl.adjoint(dr, dT)
-    if heights is None:
-        assert all(torch.equal(got[k], ref[k]) for k in FIELDS)
-    _close(got, ref)
-    # and the undecomposed monolithic adjoint to rounding
-    _close(got, sim.adjoint(dr, dT))
+    mono = sim.adjoint(dr, dT)
+    _equal(ref, mono)
+    if heights is None:  # whole tiles: bitwise the undecomposed dvbm_adjoint
+        assert all(torch.equal(got[k], mono[k]) for k in FIELDS)
+    _close(got, mono)
     sl.close()
     sim.close()
 

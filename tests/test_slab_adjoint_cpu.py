@@ -17,7 +17,7 @@ import torch.distributed as dist
 import torch.multiprocessing as mp
 
 NPOP, NX, ROWS = 3, 4, 5
-ACTIONS = [1, 1, 1, 2, 2, 2, 1, 1, 2, 2, 0]  # restore, recompute..., adjoint steps..., done
+ACTIONS = [1, 1, 3, 1, 3, 2, 2, 1, 1, 3, 2, 0]  # restore, recompute + code rows ..., adjoint steps ..., done
 
 
 class FakeBand:

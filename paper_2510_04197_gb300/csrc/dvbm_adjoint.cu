@@ -627,8 +627,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_local(const double* __restri
 // (periodic neighbours wrap), so X is not read at all.  A band of a
 // slab-decomposed grid passes the neighbouring bands' code rows next to its
 // edges (glo: the row below y = 0, ghi: the row above y = Ny - 1; [NPOP][Nx]
-// each) instead of wrapping in y.
-template <bool RAT, bool CODED>
+// each) instead of wrapping in y (BAND).
+template <bool RAT, bool CODED, bool BAND = false>
 __global__ void __launch_bounds__(256) k_adjoint_adv(const double* __restrict__ X, const double* __restrict__ Lin,
                                                      double* __restrict__ Lout,
                                                      const unsigned char* __restrict__ codes, Geom G, Phys P,
@@ -655,8 +655,9 @@ __global__ void __launch_bounds__(256) k_adjoint_adv(const double* __restrict__ 
     }
     if (sy != 0) {
       const int ym = y == 0 ? G.Ny - 1 : y - 1, yp = y == G.Ny - 1 ? 0 : y + 1;
-      const unsigned char* pm = (y == 0 && glo) ? glo + (long long)c * G.Nx + x : cp + (long long)ym * G.Nx + x;
-      const unsigned char* pp = (y == G.Ny - 1 && ghi) ? ghi + (long long)c * G.Nx + x : cp + (long long)yp * G.Nx + x;
+      const unsigned char* pm = (BAND && y == 0 && glo) ? glo + (long long)c * G.Nx + x : cp + (long long)ym * G.Nx + x;
+      const unsigned char* pp =
+          (BAND && y == G.Ny - 1 && ghi) ? ghi + (long long)c * G.Nx + x : cp + (long long)yp * G.Nx + x;
       const int bm = (__ldg(pm) >> 2) & 3, b0 = (__ldg(cp + row + x) >> 2) & 3, bp = (__ldg(pp) >> 2) & 3;
       v = fma(-P.kyr[qn], adjoint_combine_rat(lc, G.pitch, bm, b0, bp, P.lp, P.lq, sy), v);
     }
@@ -798,7 +799,9 @@ cudaError_t launch_adjoint_step(const double* X, const double* Lin, double* Lout
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid3(grid.x, grid.y, NPOP);
-  if (P.lq > 0 && codes) k_adjoint_adv<true, true><<<grid3, block, 0, st>>>(X, Lin, Lout, codes, G, P, glo, ghi);
+  if (P.lq > 0 && codes && (glo || ghi))
+    k_adjoint_adv<true, true, true><<<grid3, block, 0, st>>>(X, Lin, Lout, codes, G, P, glo, ghi);
+  else if (P.lq > 0 && codes) k_adjoint_adv<true, true><<<grid3, block, 0, st>>>(X, Lin, Lout, codes, G, P);
   else if (P.lq > 0) k_adjoint_adv<true, false><<<grid3, block, 0, st>>>(X, Lin, Lout, nullptr, G, P);
   else k_adjoint_adv<false, false><<<grid3, block, 0, st>>>(X, Lin, Lout, nullptr, G, P);
   return cudaGetLastError();
